@@ -1,0 +1,794 @@
+/*
+ * CPU oracle for the enhanced discrete PSO of Phung et al.,
+ * "Enhanced Discrete Particle Swarm Optimization Path Planning for UAV
+ * Vision-based Surface Inspection" (arXiv:1706.04399).
+ *
+ * TEST INFRASTRUCTURE ONLY.  This file is the plain, slow, single-threaded
+ * reference that the CUDA library is checked against.  Only the tests, the
+ * smoke check and the benchmark's CPU-baseline leg may load it.  It shares no
+ * code, header, table or constant generator with the CUDA path.
+ *
+ * Every step follows the paper's text in the paper's order:
+ *   - Sec. 2.3            edge costs l_ij, blocked pairs get a very large cost
+ *   - Eq. (min)           tour cost  sum l_ij lambda_ij
+ *   - Sec. 3.1            positions, velocities as transposition lists, and the
+ *                         operators x+v, x2-x1, v1 (+) v2, c.v
+ *   - Eqs. (velocity), (position)   the particle update
+ *   - Sec. 3.2.1          deterministic (back-and-forth) initialisation
+ *   - Sec. 3.2.2          random mutation
+ *   - Sec. 3.2.3          edge exchange (2-opt, best improvement)
+ *   - Fig. "pseudocode"   the enhanced DPSO loop
+ * Where the paper is silent the reading used is stated at the spot.
+ *
+ * Velocities are kept as literal transposition lists, as in Sec. 3.1 (the CUDA
+ * path stores the permutation a list induces instead; the two agree exactly).
+ *
+ * Parity is pinned for: Philox (published known-answer vectors), the cost
+ * matrix (hand-checkable integer grid values, exact dyadic blocking), the
+ * operators (the Sec. 3.1 worked example and the algebraic definitions),
+ * fitness (brute force over all tours for n <= 9 and closed-form grid optima),
+ * 2-opt (2-optimality and per-move fitness deltas), mutation (kept particles
+ * unchanged, disturbed count) and the loop (monotone gbest history, gbest =
+ * min pbest, valid permutations).  The full stochastic trajectory has no
+ * closed form: beyond those invariants it is "parity unpinned".
+ */
+#include <math.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#define ORC_DET_INIT 1
+#define ORC_MUTATION 2
+#define ORC_TWO_OPT 4
+
+#define ORC_ERR_ARG (-1)
+#define ORC_ERR_RANGE (-2)
+#define ORC_ERR_MEM (-3)
+
+#define ORC_COST_MAX (1 << 29)
+
+/* ------------------------------------------------------------------------ */
+/* Philox4x32-10, Salmon, Moraes, Dror, Shaw, "Parallel random numbers: as   */
+/* easy as 1, 2, 3", SC'11.  Round: two 32x32->64 products of counter words */
+/* 0 and 2 with the published multipliers, outputs permuted and xor-ed with  */
+/* the key; the key is advanced by the published Weyl constants between     */
+/* rounds.                                                                   */
+/* ------------------------------------------------------------------------ */
+void orc_philox4x32_10(const uint32_t ctr[4], const uint32_t key[2], uint32_t out[4])
+{
+    uint32_t c0 = ctr[0], c1 = ctr[1], c2 = ctr[2], c3 = ctr[3];
+    uint32_t k0 = key[0], k1 = key[1];
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        uint64_t p0 = (uint64_t)0xD2511F53u * (uint64_t)c0;
+        uint64_t p1 = (uint64_t)0xCD9E8D57u * (uint64_t)c2;
+        uint32_t n0 = (uint32_t)(p1 >> 32) ^ c1 ^ k0;
+        uint32_t n1 = (uint32_t)p1;
+        uint32_t n2 = (uint32_t)(p0 >> 32) ^ c3 ^ k1;
+        uint32_t n3 = (uint32_t)p0;
+        c0 = n0; c1 = n1; c2 = n2; c3 = n3;
+    }
+    out[0] = c0; out[1] = c1; out[2] = c2; out[3] = c3;
+}
+
+/* One 32-bit draw.  Counter = (draw/4, particle, iteration, phase), key =
+ * the 64-bit seed split into halves; the draw takes output word draw%4.
+ * Phases: 1 = initial permutation, 2 = velocity coefficients, 3 = mutation. */
+uint32_t orc_draw(uint64_t seed, uint32_t phase, uint32_t iter, uint32_t particle,
+                  uint32_t draw)
+{
+    uint32_t ctr[4] = {draw >> 2, particle, iter, phase};
+    uint32_t key[2] = {(uint32_t)seed, (uint32_t)(seed >> 32)};
+    uint32_t out[4];
+    orc_philox4x32_10(ctr, key, out);
+    return out[draw & 3u];
+}
+
+/* Integer in [0, m) from a 32-bit draw: multiply-shift without rejection. */
+static uint32_t bounded(uint32_t u, uint32_t m)
+{
+    return (uint32_t)(((uint64_t)u * (uint64_t)m) >> 32);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.3: edge length l_ij between viewpoints.  Reading: the straight    */
+/* segment's Euclidean length in millimetres, rounded to nearest (ties to    */
+/* even) in FP64, plus a fixed penalty when the closed segment meets any     */
+/* obstacle box grown by the UAV radius (the "very large cost" of a blocked  */
+/* pair; the Sec. 2.2 voxel inflation made axis-aligned).                    */
+/* ------------------------------------------------------------------------ */
+
+/* Slab test of the closed segment p + t (q - p), t in [0,1], against the
+ * closed box [lo - r, hi + r]. */
+int orc_segment_blocked(const double *p, const double *q, const double *box, double r)
+{
+    double tmin = 0.0, tmax = 1.0;
+    for (int k = 0; k < 3; ++k) {
+        double lo = box[k] - r;
+        double hi = box[3 + k] + r;
+        double d = q[k] - p[k];
+        if (d == 0.0) {
+            if (p[k] < lo || p[k] > hi)
+                return 0;
+        } else {
+            double t1 = (lo - p[k]) / d;
+            double t2 = (hi - p[k]) / d;
+            if (t1 > t2) {
+                double t = t1;
+                t1 = t2;
+                t2 = t;
+            }
+            if (t1 > tmin)
+                tmin = t1;
+            if (t2 < tmax)
+                tmax = t2;
+        }
+    }
+    return tmin <= tmax;
+}
+
+/* C[i][j] for i<j, mirrored; zero diagonal.  Returns ORC_ERR_RANGE when an
+ * entry exceeds 2^29 (the fixed-point range the integer deltas rely on). */
+int orc_cost_matrix(const double *xyz, int32_t n, const double *boxes, int32_t m,
+                    double radius, int32_t penalty, int32_t *C)
+{
+    if (n < 1 || m < 0 || penalty < 0)
+        return ORC_ERR_ARG;
+    int status = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        C[(int64_t)i * n + i] = 0;
+        for (int32_t j = i + 1; j < n; ++j) {
+            const double *p = xyz + 3 * (int64_t)i;
+            const double *q = xyz + 3 * (int64_t)j;
+            double dx = q[0] - p[0];
+            double dy = q[1] - p[1];
+            double dz = q[2] - p[2];
+            double s = dx * dx;
+            s = s + dy * dy;
+            s = s + dz * dz;
+            double dist = sqrt(s);
+            long long mm = llrint(1000.0 * dist);
+            int blocked = 0;
+            for (int32_t b = 0; b < m && !blocked; ++b)
+                blocked = orc_segment_blocked(p, q, boxes + 6 * (int64_t)b, radius);
+            long long v = mm + (blocked ? (long long)penalty : 0);
+            if (v > ORC_COST_MAX) {
+                status = ORC_ERR_RANGE;
+                v = ORC_COST_MAX;
+            }
+            C[(int64_t)i * n + j] = (int32_t)v;
+            C[(int64_t)j * n + i] = (int32_t)v;
+        }
+    }
+    return status;
+}
+
+/* Eq. (min) for the tour x (closing edge included). */
+int64_t orc_fitness(const int32_t *C, int32_t n, const uint16_t *x)
+{
+    int64_t f = 0;
+    for (int32_t k = 0; k < n; ++k)
+        f += C[(int64_t)x[k] * n + x[(k + 1) % n]];
+    return f;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.1 operators.  A velocity is a list of transpositions of node      */
+/* LABELS (the worked example (1,4,2,3,5,1)+((1,2),(2,3)) = (3,4,1,2,5,3)    */
+/* changes n_1 itself, so a transposition swaps labels wherever they sit).   */
+/* Lists are stored as 2*len uint16 values (a0,b0,a1,b1,...).               */
+/* ------------------------------------------------------------------------ */
+
+/* x + v: apply the transpositions in order. */
+void orc_apply(uint16_t *x, int32_t n, const uint16_t *v, int64_t len)
+{
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    for (int32_t k = 0; k < n; ++k)
+        pos[x[k]] = k;
+    for (int64_t e = 0; e < len; ++e) {
+        uint16_t a = v[2 * e], b = v[2 * e + 1];
+        int32_t pa = pos[a], pb = pos[b];
+        x[pa] = b;
+        x[pb] = a;
+        pos[a] = pb;
+        pos[b] = pa;
+    }
+    free(pos);
+}
+
+/* x2 - x1: the velocity v with x1 + v = x2.  Reading (the paper only states
+ * the property): scan positions left to right and, where the running copy of
+ * x1 differs from x2, emit the transposition (current label, wanted label).
+ * This yields n - cycles(x2 o x1^-1) transpositions, the minimum.  v_out needs
+ * room for 2*(n-1) values.  Returns the length. */
+int64_t orc_subtract(const uint16_t *x2, const uint16_t *x1, int32_t n, uint16_t *v_out)
+{
+    uint16_t *y = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+    int32_t *pos = (int32_t *)malloc(sizeof(int32_t) * (size_t)n);
+    memcpy(y, x1, sizeof(uint16_t) * (size_t)n);
+    for (int32_t k = 0; k < n; ++k)
+        pos[y[k]] = k;
+    int64_t len = 0;
+    for (int32_t k = 0; k < n; ++k) {
+        if (y[k] != x2[k]) {
+            uint16_t a = y[k], b = x2[k];
+            v_out[2 * len] = a;
+            v_out[2 * len + 1] = b;
+            ++len;
+            /* the transposition (a b) applied to y: a sits at k, b at pos[b] */
+            int32_t pb = pos[b];
+            y[k] = b;
+            y[pb] = a;
+            pos[b] = k;
+            pos[a] = pb;
+        }
+    }
+    free(pos);
+    free(y);
+    return len;
+}
+
+/* c.v keeps the first floor(c |v|) transpositions (Sec. 3.1, 0 < c <= 1).
+ * Reading for the rounding: c = phi * r with r = u / 2^32, evaluated in
+ * fixed point: cq = (phi_q u) >> 32 with phi_q = round(phi 2^32), then
+ * k = (cq |v|) >> 32. */
+static uint64_t fixed_q32(double c)
+{
+    return (uint64_t)llround(ldexp(c, 32));
+}
+
+static int64_t scaled_count(uint64_t phi_q, uint32_t u, int64_t len)
+{
+    uint64_t cq = (phi_q * (uint64_t)u) >> 32;
+    return (int64_t)((cq * (uint64_t)len) >> 32);
+}
+
+/* Length kept by (phi r).v for a list of length len (exported for tests). */
+int64_t orc_scaled_count(double phi, uint32_t u, int64_t len)
+{
+    return scaled_count(fixed_q32(phi), u, len);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.2.1 deterministic initialisation: back-and-forth tours over the    */
+/* grid tags.  Reading: variant s in 0..7 -- bit0 walks lines along columns  */
+/* instead of rows, bit1 visits lines in descending order, bit2 flips the    */
+/* direction of even lines; line L is walked forward iff (L odd) == bit2.    */
+/* Faces are concatenated in ascending face id.                              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    int32_t face, line, pos, node;
+} orc_key;
+
+static int key_cmp(const void *pa, const void *pb)
+{
+    const orc_key *a = (const orc_key *)pa, *b = (const orc_key *)pb;
+    if (a->face != b->face)
+        return a->face < b->face ? -1 : 1;
+    if (a->line != b->line)
+        return a->line < b->line ? -1 : 1;
+    if (a->pos != b->pos)
+        return a->pos < b->pos ? -1 : 1;
+    return 0;
+}
+
+/* Back-and-forth order of variant s (0..7).  Returns ORC_ERR_ARG when tags
+ * are negative or not unique. */
+int orc_boustrophedon(const int32_t *tags, int32_t n, int32_t s, uint16_t *order)
+{
+    orc_key *k = (orc_key *)malloc(sizeof(orc_key) * (size_t)n);
+    int bad = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        int32_t face = tags[3 * i], row = tags[3 * i + 1], col = tags[3 * i + 2];
+        if (face < 0 || row < 0 || col < 0)
+            bad = 1;
+        int32_t line = (s & 1) ? col : row;
+        int32_t pos = (s & 1) ? row : col;
+        int backward = ((line & 1) != 0) != ((s & 4) != 0);
+        k[i].face = face;
+        k[i].line = (s & 2) ? -line : line;
+        k[i].pos = backward ? -pos : pos;
+        k[i].node = i;
+    }
+    qsort(k, (size_t)n, sizeof(orc_key), key_cmp);
+    for (int32_t i = 0; i + 1 < n; ++i)
+        if (key_cmp(&k[i], &k[i + 1]) == 0)
+            bad = 1;
+    for (int32_t i = 0; i < n; ++i)
+        order[i] = (uint16_t)k[i].node;
+    free(k);
+    return bad ? ORC_ERR_ARG : 0;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Sec. 3.2.3 edge exchange.  Every exchange of two non-adjacent edges      */
+/* (x_i,x_i+1), (x_j,x_j+1) is evaluated; the one with the largest gain is  */
+/* applied by reversing x[i+1..j]; repeated until no exchange improves.     */
+/* Ties go to the smallest (i, j).  Returns moves applied.                  */
+/* ------------------------------------------------------------------------ */
+int64_t orc_two_opt(const int32_t *C, int32_t n, uint16_t *x, int64_t *f,
+                    int32_t max_moves, int64_t *pairs_out)
+{
+    int64_t moves = 0, pairs = 0;
+    for (;;) {
+        if (max_moves > 0 && moves >= max_moves)
+            break;
+        int64_t best = 0;
+        int32_t bi = -1, bj = -1;
+        for (int32_t i = 0; i < n; ++i) {
+            for (int32_t j = i + 2; j < n; ++j) {
+                if (i == 0 && j == n - 1)
+                    continue;
+                int32_t a = x[i], b = x[i + 1], c = x[j], d = x[(j + 1) % n];
+                int64_t delta = (int64_t)C[(int64_t)a * n + c] + C[(int64_t)b * n + d]
+                                - C[(int64_t)a * n + b] - C[(int64_t)c * n + d];
+                ++pairs;
+                if (delta < best) {
+                    best = delta;
+                    bi = i;
+                    bj = j;
+                }
+            }
+        }
+        if (bi < 0)
+            break;
+        for (int32_t lo = bi + 1, hi = bj; lo < hi; ++lo, --hi) {
+            uint16_t t = x[lo];
+            x[lo] = x[hi];
+            x[hi] = t;
+        }
+        *f += best;
+        ++moves;
+    }
+    if (pairs_out)
+        *pairs_out += pairs;
+    return moves;
+}
+
+/* ------------------------------------------------------------------------ */
+/* The swarm and the loop of Fig. "pseudocode".                              */
+/* ------------------------------------------------------------------------ */
+typedef struct {
+    uint16_t *t; /* 2*len labels */
+    int64_t len, cap;
+} orc_vel;
+
+typedef struct {
+    int32_t n, S;
+    int32_t *C;
+    double w, phi1, phi2;
+    int32_t mut_period, mut_swaps, det_frac_pct, stall_limit, flags, trigger, max_moves;
+    uint64_t seed;
+    uint16_t *X, *P, *G;
+    int64_t *F, *PF, gf;
+    orc_vel *V;
+    int32_t t, stall, done;
+    int64_t *hist;
+    int32_t hist_len, hist_cap;
+    int64_t pairs, moves, two_opt_runs;
+    int32_t last_improved, last_two_opt;
+    uint16_t *scratch; /* 2*(n-1) transpositions */
+} orc_swarm;
+
+static int vel_reserve(orc_vel *v, int64_t len)
+{
+    if (len <= v->cap)
+        return 0;
+    int64_t cap = v->cap ? v->cap : 16;
+    while (cap < len)
+        cap *= 2;
+    uint16_t *t = (uint16_t *)realloc(v->t, sizeof(uint16_t) * 2 * (size_t)cap);
+    if (!t)
+        return ORC_ERR_MEM;
+    v->t = t;
+    v->cap = cap;
+    return 0;
+}
+
+static int vel_append(orc_vel *v, const uint16_t *t, int64_t len)
+{
+    if (vel_reserve(v, v->len + len))
+        return ORC_ERR_MEM;
+    memcpy(v->t + 2 * v->len, t, sizeof(uint16_t) * 2 * (size_t)len);
+    v->len += len;
+    return 0;
+}
+
+void orc_swarm_free(orc_swarm *sw)
+{
+    if (!sw)
+        return;
+    if (sw->V)
+        for (int32_t p = 0; p < sw->S; ++p)
+            free(sw->V[p].t);
+    free(sw->V);
+    free(sw->C);
+    free(sw->X);
+    free(sw->P);
+    free(sw->G);
+    free(sw->F);
+    free(sw->PF);
+    free(sw->hist);
+    free(sw->scratch);
+    free(sw);
+}
+
+static uint16_t *row_of(uint16_t *A, int32_t n, int32_t p)
+{
+    return A + (int64_t)p * n;
+}
+
+/* gbest = the particle with the smallest (pbest fitness, index); the
+ * swarm's best is replaced only on strict improvement (Fig. "pseudocode"). */
+void orc_swarm_gbest(orc_swarm *sw)
+{
+    int32_t bp = 0;
+    for (int32_t p = 1; p < sw->S; ++p)
+        if (sw->PF[p] < sw->PF[bp])
+            bp = p;
+    if (sw->PF[bp] < sw->gf) {
+        sw->gf = sw->PF[bp];
+        memcpy(sw->G, row_of(sw->P, sw->n, bp), sizeof(uint16_t) * (size_t)sw->n);
+    }
+}
+
+static void pbest(orc_swarm *sw, int32_t p)
+{
+    if (sw->F[p] < sw->PF[p]) {
+        sw->PF[p] = sw->F[p];
+        memcpy(row_of(sw->P, sw->n, p), row_of(sw->X, sw->n, p),
+               sizeof(uint16_t) * (size_t)sw->n);
+    }
+}
+
+/* Initialisation block of Fig. "pseudocode": positions (some back-and-forth,
+ * the rest random), fitness, pbest = itself, empty velocity, gbest.
+ * Reading of "10% specific": n_det = max(1, floor(S * pct / 100)) particles
+ * take variant p%8 rotated left by floor(p/8); the others are Fisher-Yates
+ * shuffles of the identity driven by phase-1 draws. */
+orc_swarm *orc_swarm_new(const int32_t *C, int32_t n, const int32_t *tags, int32_t S,
+                         double w, double phi1, double phi2, int32_t mut_period,
+                         int32_t mut_swaps, int32_t det_frac_pct, int32_t stall_limit,
+                         int32_t flags, int32_t trigger, int32_t max_moves, uint64_t seed,
+                         int32_t *status)
+{
+    *status = 0;
+    if (n < 3 || n > 65535 || S < 1 || S > 65535 || !(w >= 0.0 && w <= 1.0) ||
+        !(phi1 >= 0.0 && phi1 <= 1.0) || !(phi2 >= 0.0 && phi2 <= 1.0) || mut_period < 1 ||
+        mut_swaps < 0 || det_frac_pct < 0 || det_frac_pct > 100 || stall_limit < 0 ||
+        max_moves < 0 || trigger < 0 || trigger > 1) {
+        *status = ORC_ERR_ARG;
+        return NULL;
+    }
+    orc_swarm *sw = (orc_swarm *)calloc(1, sizeof(orc_swarm));
+    sw->n = n;
+    sw->S = S;
+    sw->w = w;
+    sw->phi1 = phi1;
+    sw->phi2 = phi2;
+    sw->mut_period = mut_period;
+    sw->mut_swaps = mut_swaps;
+    sw->det_frac_pct = det_frac_pct;
+    sw->stall_limit = stall_limit;
+    sw->flags = flags;
+    sw->trigger = trigger;
+    sw->max_moves = max_moves;
+    sw->seed = seed;
+    size_t nn = (size_t)n * (size_t)n;
+    sw->C = (int32_t *)malloc(sizeof(int32_t) * nn);
+    memcpy(sw->C, C, sizeof(int32_t) * nn);
+    sw->X = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n * (size_t)S);
+    sw->P = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n * (size_t)S);
+    sw->G = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+    sw->F = (int64_t *)malloc(sizeof(int64_t) * (size_t)S);
+    sw->PF = (int64_t *)malloc(sizeof(int64_t) * (size_t)S);
+    sw->V = (orc_vel *)calloc((size_t)S, sizeof(orc_vel));
+    sw->scratch = (uint16_t *)malloc(sizeof(uint16_t) * 2 * (size_t)n);
+    sw->hist_cap = 64;
+    sw->hist = (int64_t *)malloc(sizeof(int64_t) * (size_t)sw->hist_cap);
+
+    int32_t n_det = 0;
+    if ((flags & ORC_DET_INIT) && tags) {
+        n_det = (int32_t)(((int64_t)S * det_frac_pct) / 100);
+        if (n_det < 1)
+            n_det = 1;
+        if (n_det > S)
+            n_det = S;
+    }
+    uint16_t *orders = (uint16_t *)malloc(sizeof(uint16_t) * 8 * (size_t)n);
+    if (n_det > 0) {
+        for (int32_t s = 0; s < 8; ++s) {
+            if (orc_boustrophedon(tags, n, s, orders + (int64_t)s * n) != 0) {
+                *status = ORC_ERR_ARG;
+                free(orders);
+                orc_swarm_free(sw);
+                return NULL;
+            }
+        }
+    }
+    for (int32_t p = 0; p < S; ++p) {
+        uint16_t *x = row_of(sw->X, n, p);
+        if (p < n_det) {
+            const uint16_t *ord = orders + (int64_t)(p % 8) * n;
+            int32_t rot = (p / 8) % n;
+            for (int32_t k = 0; k < n; ++k)
+                x[k] = ord[(k + rot) % n];
+        } else {
+            for (int32_t k = 0; k < n; ++k)
+                x[k] = (uint16_t)k;
+            for (int32_t i = n - 1; i >= 1; --i) {
+                uint32_t u = orc_draw(seed, 1, 0, (uint32_t)p, (uint32_t)(n - 1 - i));
+                int32_t j = (int32_t)bounded(u, (uint32_t)(i + 1));
+                uint16_t t = x[i];
+                x[i] = x[j];
+                x[j] = t;
+            }
+        }
+        sw->F[p] = orc_fitness(sw->C, n, x);
+        sw->PF[p] = sw->F[p];
+        memcpy(row_of(sw->P, n, p), x, sizeof(uint16_t) * (size_t)n);
+        sw->V[p].len = 0;
+    }
+    free(orders);
+    int32_t bp = 0;
+    for (int32_t p = 1; p < S; ++p)
+        if (sw->F[p] < sw->F[bp])
+            bp = p;
+    sw->gf = sw->F[bp];
+    memcpy(sw->G, row_of(sw->X, n, bp), sizeof(uint16_t) * (size_t)n);
+    return sw;
+}
+
+/* Eqs. (velocity) and (position) for one particle, against the gbest G0 of
+ * the start of the iteration (the gbest is updated after the particle loop,
+ * Fig. "pseudocode").  v <- w.v (+) phi1 r1.(P - x) (+) phi2 r2.(G - x);
+ * x <- x + v; fitness; pbest on strict improvement.  r1, r2 are one draw
+ * each per particle per iteration (phase 2, draws 0 and 1).  With w = 1 the
+ * list is kept whole; for w < 1 it is first replaced by the canonical list of
+ * the permutation it induces, (identity + v) - identity, and then truncated. */
+static int move_particle(orc_swarm *sw, int32_t p, int32_t t, const uint16_t *G0)
+{
+    int32_t n = sw->n;
+    uint16_t *x = row_of(sw->X, n, p);
+    orc_vel *v = &sw->V[p];
+    uint32_t u1 = orc_draw(sw->seed, 2, (uint32_t)t, (uint32_t)p, 0);
+    uint32_t u2 = orc_draw(sw->seed, 2, (uint32_t)t, (uint32_t)p, 1);
+    uint64_t w_q = fixed_q32(sw->w);
+
+    if (w_q < ((uint64_t)1 << 32)) {
+        uint16_t *id = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+        for (int32_t k = 0; k < n; ++k)
+            id[k] = (uint16_t)k;
+        uint16_t *perm = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+        memcpy(perm, id, sizeof(uint16_t) * (size_t)n);
+        orc_apply(perm, n, v->t, v->len);
+        int64_t len = orc_subtract(perm, id, n, sw->scratch);
+        int64_t keep = (int64_t)((w_q * (uint64_t)len) >> 32);
+        v->len = 0;
+        if (vel_append(v, sw->scratch, keep))
+            return ORC_ERR_MEM;
+        free(perm);
+        free(id);
+    }
+
+    int64_t la = orc_subtract(row_of(sw->P, n, p), x, n, sw->scratch);
+    int64_t ka = scaled_count(fixed_q32(sw->phi1), u1, la);
+    if (vel_append(v, sw->scratch, ka))
+        return ORC_ERR_MEM;
+    int64_t lb = orc_subtract(G0, x, n, sw->scratch);
+    int64_t kb = scaled_count(fixed_q32(sw->phi2), u2, lb);
+    if (vel_append(v, sw->scratch, kb))
+        return ORC_ERR_MEM;
+
+    orc_apply(x, n, v->t, v->len);
+    sw->F[p] = orc_fitness(sw->C, n, x);
+    pbest(sw, p);
+    return 0;
+}
+
+int orc_swarm_move(orc_swarm *sw, int32_t t)
+{
+    uint16_t *G0 = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)sw->n);
+    memcpy(G0, sw->G, sizeof(uint16_t) * (size_t)sw->n);
+    int st = 0;
+    for (int32_t p = 0; p < sw->S && !st; ++p)
+        st = move_particle(sw, p, t, G0);
+    free(G0);
+    return st;
+}
+
+/* Sec. 3.2.2 random mutation.  Readings: particles are ordered by (fitness,
+ * index); a particle is identical to an earlier one in that order when the
+ * tour arrays are equal; the first ceil(S/3) distinct particles are kept and
+ * every other particle is disturbed by mut_swaps swaps of two distinct
+ * positions (phase-3 draws 2q, 2q+1), its velocity emptied, then re-scored
+ * and its pbest updated.  kept_out (may be NULL) receives 1 for kept. */
+typedef struct {
+    int64_t f;
+    int32_t p;
+} orc_fi;
+
+static int fi_cmp(const void *pa, const void *pb)
+{
+    const orc_fi *a = (const orc_fi *)pa, *b = (const orc_fi *)pb;
+    if (a->f != b->f)
+        return a->f < b->f ? -1 : 1;
+    return a->p < b->p ? -1 : (a->p > b->p);
+}
+
+int orc_swarm_mutate(orc_swarm *sw, int32_t t, int32_t *kept_out)
+{
+    int32_t n = sw->n, S = sw->S;
+    orc_fi *ord = (orc_fi *)malloc(sizeof(orc_fi) * (size_t)S);
+    for (int32_t p = 0; p < S; ++p) {
+        ord[p].f = sw->F[p];
+        ord[p].p = p;
+    }
+    qsort(ord, (size_t)S, sizeof(orc_fi), fi_cmp);
+    int32_t *kept = (int32_t *)calloc((size_t)S, sizeof(int32_t));
+    int32_t K = (S + 2) / 3, nkept = 0;
+    for (int32_t r = 0; r < S; ++r) {
+        int32_t p = ord[r].p;
+        int dup = 0;
+        for (int32_t q = r - 1; q >= 0 && ord[q].f == ord[r].f && !dup; --q)
+            dup = memcmp(row_of(sw->X, n, ord[q].p), row_of(sw->X, n, p),
+                         sizeof(uint16_t) * (size_t)n) == 0;
+        if (!dup && nkept < K) {
+            kept[p] = 1;
+            ++nkept;
+        }
+    }
+    for (int32_t p = 0; p < S; ++p) {
+        if (kept[p])
+            continue;
+        uint16_t *x = row_of(sw->X, n, p);
+        for (int32_t q = 0; q < sw->mut_swaps; ++q) {
+            uint32_t ui = orc_draw(sw->seed, 3, (uint32_t)t, (uint32_t)p, (uint32_t)(2 * q));
+            uint32_t uj = orc_draw(sw->seed, 3, (uint32_t)t, (uint32_t)p, (uint32_t)(2 * q + 1));
+            int32_t i = (int32_t)bounded(ui, (uint32_t)n);
+            int32_t j = (int32_t)bounded(uj, (uint32_t)(n - 1));
+            if (j >= i)
+                ++j;
+            uint16_t tmp = x[i];
+            x[i] = x[j];
+            x[j] = tmp;
+        }
+        sw->V[p].len = 0;
+        sw->F[p] = orc_fitness(sw->C, n, x);
+        pbest(sw, p);
+    }
+    if (kept_out)
+        memcpy(kept_out, kept, sizeof(int32_t) * (size_t)S);
+    free(kept);
+    free(ord);
+    return 0;
+}
+
+/* Edge exchange on a subset of particles (all when idx == NULL), then pbest. */
+void orc_swarm_two_opt(orc_swarm *sw, const int32_t *idx, int32_t count)
+{
+    int32_t total = idx ? count : sw->S;
+    for (int32_t r = 0; r < total; ++r) {
+        int32_t p = idx ? idx[r] : r;
+        sw->moves += orc_two_opt(sw->C, sw->n, row_of(sw->X, sw->n, p), &sw->F[p],
+                                 sw->max_moves, &sw->pairs);
+        pbest(sw, p);
+    }
+}
+
+static void hist_put(orc_swarm *sw, int32_t t, int64_t v)
+{
+    if (t > sw->hist_cap) {
+        while (sw->hist_cap < t)
+            sw->hist_cap *= 2;
+        sw->hist = (int64_t *)realloc(sw->hist, sizeof(int64_t) * (size_t)sw->hist_cap);
+    }
+    sw->hist[t - 1] = v;
+    if (t > sw->hist_len)
+        sw->hist_len = t;
+}
+
+/* One generation of Fig. "pseudocode": move all particles, mutate every
+ * mut_period-th generation, update gbest, and run the edge exchange when the
+ * gbest did not strictly improve in this generation (trigger 0), or only in
+ * mutation generations that did not improve it (trigger 1, the wording of
+ * Sec. 4).  Returns 1 when the loop has stopped (stall limit), else 0. */
+int orc_swarm_iterate(orc_swarm *sw)
+{
+    if (sw->done)
+        return 1;
+    int32_t t = sw->t + 1;
+    int64_t gf0 = sw->gf;
+    int st = orc_swarm_move(sw, t);
+    if (st)
+        return st;
+    int mut = (sw->flags & ORC_MUTATION) && (t % sw->mut_period == 0);
+    if (mut)
+        orc_swarm_mutate(sw, t, NULL);
+    orc_swarm_gbest(sw);
+    int improved = sw->gf < gf0;
+    hist_put(sw, t, sw->gf);
+    int run2 = (sw->flags & ORC_TWO_OPT) && !improved && (sw->trigger == 0 || mut);
+    sw->last_two_opt = run2;
+    if (run2) {
+        orc_swarm_two_opt(sw, NULL, 0);
+        sw->two_opt_runs += 1;
+        orc_swarm_gbest(sw);
+        hist_put(sw, t, sw->gf);
+        improved = sw->gf < gf0;
+    }
+    sw->last_improved = improved;
+    sw->stall = improved ? 0 : sw->stall + 1;
+    sw->t = t;
+    if (sw->stall_limit > 0 && sw->stall >= sw->stall_limit)
+        sw->done = 1;
+    return 0;
+}
+
+int orc_swarm_run(orc_swarm *sw, int32_t iterations)
+{
+    for (int32_t k = 0; k < iterations; ++k) {
+        int st = orc_swarm_iterate(sw);
+        if (st < 0)
+            return st;
+        if (sw->done)
+            break;
+    }
+    return 0;
+}
+
+/* ---- accessors for the Python wrapper ---- */
+int32_t orc_swarm_n(const orc_swarm *sw) { return sw->n; }
+int32_t orc_swarm_size(const orc_swarm *sw) { return sw->S; }
+int32_t orc_swarm_t(const orc_swarm *sw) { return sw->t; }
+int32_t orc_swarm_done(const orc_swarm *sw) { return sw->done; }
+int32_t orc_swarm_stall(const orc_swarm *sw) { return sw->stall; }
+int64_t orc_swarm_gf(const orc_swarm *sw) { return sw->gf; }
+int32_t orc_swarm_last_two_opt(const orc_swarm *sw) { return sw->last_two_opt; }
+int32_t orc_swarm_last_improved(const orc_swarm *sw) { return sw->last_improved; }
+
+void orc_swarm_counters(const orc_swarm *sw, int64_t out[3])
+{
+    out[0] = sw->pairs;
+    out[1] = sw->moves;
+    out[2] = sw->two_opt_runs;
+}
+
+/* Copies out X, P (S*n), G (n), F, PF (S), and V as the permutation each list
+ * induces on the identity (S*n).  Any pointer may be NULL. */
+void orc_swarm_export(const orc_swarm *sw, uint16_t *X, uint16_t *P, uint16_t *G,
+                      int64_t *F, int64_t *PF, uint16_t *Vperm)
+{
+    size_t sn = (size_t)sw->S * (size_t)sw->n;
+    if (X)
+        memcpy(X, sw->X, sizeof(uint16_t) * sn);
+    if (P)
+        memcpy(P, sw->P, sizeof(uint16_t) * sn);
+    if (G)
+        memcpy(G, sw->G, sizeof(uint16_t) * (size_t)sw->n);
+    if (F)
+        memcpy(F, sw->F, sizeof(int64_t) * (size_t)sw->S);
+    if (PF)
+        memcpy(PF, sw->PF, sizeof(int64_t) * (size_t)sw->S);
+    if (Vperm) {
+        for (int32_t p = 0; p < sw->S; ++p) {
+            uint16_t *y = Vperm + (int64_t)p * sw->n;
+            for (int32_t k = 0; k < sw->n; ++k)
+                y[k] = (uint16_t)k;
+            orc_apply(y, sw->n, sw->V[p].t, sw->V[p].len);
+        }
+    }
+}
+
+int64_t orc_swarm_vel_len(const orc_swarm *sw, int32_t p) { return sw->V[p].len; }
+
+int32_t orc_swarm_history(const orc_swarm *sw, int64_t *out, int32_t cap)
+{
+    int32_t k = sw->hist_len < cap ? sw->hist_len : cap;
+    if (out && k > 0)
+        memcpy(out, sw->hist, sizeof(int64_t) * (size_t)k);
+    return sw->hist_len;
+}

@@ -1,0 +1,217 @@
+/*
+ * dpso.h -- C ABI of the GB300 library for the enhanced discrete particle swarm
+ * optimisation (DPSO) of Phung, Quach, Dinh, Ha, "Enhanced Discrete Particle
+ * Swarm Optimization Path Planning for UAV Vision-based Surface Inspection"
+ * (arXiv:1706.04399).
+ *
+ * The inspection path is the extended travelling-salesman tour of Sec. 2.3
+ * over camera viewpoints: Eq. (min) under the degree and no-subtour
+ * constraints.  The solver is the DPSO of Sec. 3 and Fig. "pseudocode":
+ * swap-sequence velocities (Sec. 3.1), deterministic initialisation
+ * (Sec. 3.2.1), random mutation (Sec. 3.2.2) and edge exchange (Sec. 3.2.3),
+ * with the particles evolved in parallel on the GPU (Sec. 3.2.4).
+ *
+ * Conventions for every call:
+ *   - Return value: DPSO_OK (0) on success, else a negative DPSO_ERR_* code.
+ *     No C++ exception crosses this boundary.
+ *   - A pointer named *_dev is a CUDA device pointer on the current device (for
+ *     example a torch tensor's data_ptr()); *_host is ordinary host memory.
+ *   - `stream` is a cudaStream_t passed as void*; NULL means the legacy
+ *     default stream.  Asynchronous calls only enqueue work on it; the caller
+ *     keeps their input buffers alive until the stream has passed the call.
+ *   - Tours are permutations of 0..n-1 without the closing copy of the first
+ *     node (Sec. 3.1 stores n_{N+1} = n_1; here it is implied).
+ *   - Costs are integer millimetres (int32 per edge, int64 per tour).
+ *   - Limits: 3 <= n <= DPSO_MAX_N viewpoints, 1 <= swarm <= DPSO_MAX_SWARM,
+ *     every edge cost in [0, DPSO_COST_MAX].
+ */
+#ifndef DPSO_H
+#define DPSO_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define DPSO_OK 0
+#define DPSO_ERR_ARG (-1)       /* invalid argument (sizes, NaN, duplicate tags, asymmetric C) */
+#define DPSO_ERR_RANGE (-2)     /* n or swarm above the limits, or an edge cost > DPSO_COST_MAX */
+#define DPSO_ERR_NO_MEMORY (-3) /* device allocation failed or over the memory budget */
+#define DPSO_ERR_CUDA (-4)      /* a CUDA runtime call failed */
+#define DPSO_ERR_TIMEOUT (-5)   /* a bounded device-side wait ran out */
+#define DPSO_ERR_INTERNAL (-6)  /* an internal consistency check failed */
+
+#define DPSO_MAX_N 8192
+#define DPSO_MAX_SWARM 65535
+#define DPSO_COST_MAX (1 << 29)
+
+/* dpso_params.flags */
+#define DPSO_FLAG_DET_INIT 1 /* Sec. 3.2.1 back-and-forth seeding (needs grid tags) */
+#define DPSO_FLAG_MUTATION 2 /* Sec. 3.2.2 random mutation */
+#define DPSO_FLAG_TWO_OPT 4  /* Sec. 3.2.3 edge exchange */
+
+/*
+ * Swarm parameters (Fig. "pseudocode"; Sec. 4 uses w = 1, phi1 = phi2 = 0.4,
+ * mutation every 3 generations).
+ *   w, phi1, phi2     inertial, cognitive and social coefficients of
+ *                     Eq. (velocity), each in [0, 1]
+ *   swarm             number of particles
+ *   mut_period        mutate every mut_period-th generation (>= 1)
+ *   mut_swaps         position swaps applied to each disturbed particle (>= 0)
+ *   det_frac_pct      percent of particles seeded back-and-forth (0..100);
+ *                     at least one when DPSO_FLAG_DET_INIT is set and tags given
+ *   stall_limit       stop after this many generations without a strict gbest
+ *                     improvement (0 = never)
+ *   flags             DPSO_FLAG_* bits
+ *   two_opt_trigger   0: edge exchange in every generation whose gbest did not
+ *                     strictly improve; 1: only in such mutation generations
+ *   max_moves         cap on 2-opt moves per particle per exchange (0 = none)
+ */
+typedef struct dpso_params {
+    double w, phi1, phi2;
+    int32_t swarm, mut_period, mut_swaps, det_frac_pct, stall_limit, flags,
+        two_opt_trigger, max_moves;
+} dpso_params;
+
+/*
+ * Edge-cost model (Sec. 2.3): straight-segment Euclidean length in mm, rounded
+ * to nearest in FP64, plus blocked_penalty_mm when the closed segment meets an
+ * obstacle box grown by uav_radius_m on every side (the "very large cost" of a
+ * blocked pair; Sec. 2.2's inflation by the UAV size).
+ */
+typedef struct dpso_cost_params {
+    double uav_radius_m;
+    int32_t blocked_penalty_mm;
+    int32_t reserved; /* must be 0 */
+} dpso_cost_params;
+
+/* Counters of a swarm. */
+typedef struct dpso_stats {
+    int32_t iterations;     /* generations completed */
+    int32_t stalled;        /* 1 once stall_limit stopped the loop */
+    int64_t gbest_cost;     /* current gbest tour cost */
+    int64_t two_opt_pairs;  /* 2-opt candidate pairs evaluated */
+    int64_t two_opt_moves;  /* 2-opt moves applied */
+    int64_t two_opt_runs;   /* generations in which the edge exchange ran */
+    int32_t device_status;  /* sticky device-side error code (DPSO_OK if none) */
+    int32_t reserved;
+} dpso_stats;
+
+typedef struct dpso_swarm dpso_swarm;
+
+/* Fills the defaults: w=1, phi1=phi2=0.4 (Sec. 4), swarm=100, mut_period=3,
+ * mut_swaps=2, det_frac_pct=10 (Fig. "pseudocode"), stall_limit=0, all
+ * flags, trigger 0, max_moves 0. */
+void dpso_default_params(dpso_params *p);
+/* uav_radius_m = 0, blocked_penalty_mm = 1 000 000. */
+void dpso_default_cost_params(dpso_cost_params *p);
+/* Static string for a status code. */
+const char *dpso_status_string(int status);
+
+/*
+ * Edge-cost matrix (Sec. 2.3).  xyz_dev: n x 3 float64 viewpoints (metres,
+ * row-major).  boxes_dev: m x 6 float64 boxes (lo_x, lo_y, lo_z, hi_x, hi_y,
+ * hi_z); may be NULL when m == 0.  C_dev: caller-owned n x n int32, row-major,
+ * written with C[i][j] = C[j][i] (computed for i < j) and a zero diagonal.
+ * 1 <= n <= DPSO_MAX_N.  Synchronises `stream` to report DPSO_ERR_ARG (a
+ * non-finite coordinate or lo > hi) or DPSO_ERR_RANGE (an entry above
+ * DPSO_COST_MAX; such entries are clamped to DPSO_COST_MAX).
+ */
+int dpso_cost_matrix(const double *xyz_dev, int32_t n, const double *boxes_dev, int32_t m,
+                     const dpso_cost_params *cp, int32_t *C_dev, void *stream);
+
+/*
+ * Tour cost, Eq. (min): cost_dev[t] = sum_k C[x_k][x_(k+1) mod n] for each of
+ * `count` tours.  tours_dev: count x n uint16, row-major.  C_dev: n x n int32.
+ * Asynchronous; inputs are not validated (tours must be permutations).
+ */
+int dpso_fitness(const int32_t *C_dev, int32_t n, const uint16_t *tours_dev, int32_t count,
+                 int64_t *cost_dev, void *stream);
+
+/*
+ * Edge exchange, Sec. 3.2.3: best-improvement 2-opt applied to each of `count`
+ * tours until no exchange of two non-adjacent edges shortens it (or max_moves
+ * moves, 0 = no cap).  Ties take the smallest (i, j).  tours_dev (count x n
+ * uint16) is rewritten in place; cost_dev (count int64) receives the final
+ * costs.  C_dev must be symmetric with a zero diagonal and entries in
+ * [0, DPSO_COST_MAX].  Library-allocated scratch holds the work queue and the
+ * counters.  Synchronises `stream`; pairs_host / moves_host (may be NULL)
+ * receive the candidate pairs evaluated and moves applied.
+ */
+int dpso_two_opt(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t count,
+                 int64_t *cost_dev, int32_t max_moves, int64_t *pairs_host,
+                 int64_t *moves_host, void *stream);
+
+/*
+ * Creates a swarm over the n x n cost matrix C_dev (copied; the caller may free
+ * it after the call) and runs the initialisation block of Fig. "pseudocode":
+ * positions (back-and-forth for a fraction, Sec. 3.2.1, else seeded random
+ * permutations), fitness, pbest = position, empty velocity, gbest.
+ * tags_host: n x 3 int32 (face, row, col) grid tags, non-negative and unique,
+ * or NULL (then every particle is random).  The library owns *out.
+ * Synchronises `stream`.  Errors: DPSO_ERR_ARG (parameters, tags, C not
+ * symmetric or diagonal not zero), DPSO_ERR_RANGE, DPSO_ERR_NO_MEMORY.
+ */
+int dpso_init(dpso_swarm **out, const int32_t *C_dev, int32_t n, const int32_t *tags_host,
+              const dpso_params *p, uint64_t seed, void *stream);
+
+/*
+ * Enqueues `iterations` generations of Fig. "pseudocode" on `stream`
+ * (asynchronous; replays CUDA graphs).  Generations after a stall stop are
+ * no-ops.  Calls on one swarm must be ordered (same stream, or synchronised).
+ */
+int dpso_step(dpso_swarm *s, int32_t iterations, void *stream);
+
+/* Best tour (n int32) and its cost; synchronises the swarm's last stream. */
+int dpso_get_best(dpso_swarm *s, int32_t *tour_host, int64_t *cost);
+
+/* gbest cost after each completed generation; *len receives the number of
+ * completed generations, at most `cap` values are written. */
+int dpso_get_history(dpso_swarm *s, int64_t *gbest_host, int32_t cap, int32_t *len);
+
+/* Counters; synchronises. */
+int dpso_get_stats(dpso_swarm *s, dpso_stats *st);
+
+/*
+ * Checkpoint: serialises the whole swarm (positions, velocities as
+ * permutations, pbests, fitness, gbest, generation and stall counters,
+ * counters, history) into buf.  With buf == NULL only *bytes is set to the
+ * size needed; otherwise *bytes is the buffer size on input and the size
+ * written on output.  Synchronises.
+ */
+int dpso_get_state(dpso_swarm *s, void *buf, size_t *bytes);
+
+/* Restores a checkpoint taken from a swarm with the same n, swarm size and
+ * parameters.  The random streams are counter-based, so a resumed run is
+ * bit-identical to an uninterrupted one.  Synchronises. */
+int dpso_set_state(dpso_swarm *s, const void *buf, size_t bytes);
+
+/* Frees the swarm (synchronises its stream first).  NULL is ignored. */
+void dpso_destroy(dpso_swarm *s);
+
+/*
+ * Synchronous convenience solve from host buffers: copies the inputs to the
+ * device, builds the cost matrix, initialises a swarm, runs `iterations`
+ * generations and copies the best tour (n int32) and cost back.  boxes_host
+ * may be NULL when m == 0; tags_host may be NULL.
+ */
+int dpso_plan(const double *xyz_host, int32_t n, const double *boxes_host, int32_t m,
+              const int32_t *tags_host, const dpso_cost_params *cp, const dpso_params *p,
+              uint64_t seed, int32_t iterations, int32_t *tour_host, int64_t *cost);
+
+/*
+ * Philox4x32-10 draws as the solver takes them (counter = (draw/4, particle,
+ * iteration, phase), key = the seed's two 32-bit halves, word draw%4), for
+ * `count` consecutive draws starting at draw 0: out_dev[d] for d < count.
+ * Exposed so the random stream itself can be checked.  Asynchronous.
+ */
+int dpso_philox_draws(uint64_t seed, uint32_t phase, uint32_t iteration, uint32_t particle,
+                      int32_t count, uint32_t *out_dev, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* DPSO_H */

@@ -12,6 +12,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import platform
 import subprocess
 
 import numpy as np
@@ -19,6 +20,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "dpso_oracle.c")
 _LIB = os.path.join(_HERE, "liboracle_dpso.so")
+_STAMP = _LIB + ".machine"
 
 DET_INIT = 1
 MUTATION = 2
@@ -31,12 +33,20 @@ ERR_RANGE = -2
 
 def build(force: bool = False) -> str:
     """Compile the oracle with strict IEEE semantics (no contraction, no fast-math)."""
-    if force or not os.path.exists(_LIB) or os.path.getmtime(_LIB) < os.path.getmtime(_SRC):
+    try:
+        with open(_STAMP) as fh:
+            same_machine = fh.read().strip() == platform.machine()
+    except OSError:
+        same_machine = False
+    if (force or not same_machine or not os.path.exists(_LIB)
+            or os.path.getmtime(_LIB) < os.path.getmtime(_SRC)):
         tmp = _LIB + f".{os.getpid()}.tmp"
         subprocess.check_call([
             "gcc", "-std=c11", "-O2", "-ffp-contract=off", "-fno-fast-math",
             "-fPIC", "-shared", "-o", tmp, _SRC, "-lm"])
         os.replace(tmp, _LIB)
+        with open(_STAMP, "w") as fh:
+            fh.write(platform.machine() + "\n")
     return _LIB
 
 
@@ -56,6 +66,7 @@ def lib():
         L.orc_philox4x32_10.argtypes = [_u32p, _u32p, _u32p]
         L.orc_draw.argtypes = [ctypes.c_uint64] + [ctypes.c_uint32] * 4
         L.orc_draw.restype = ctypes.c_uint32
+        L.orc_draws.argtypes = [ctypes.c_uint64] + [ctypes.c_uint32] * 3 + [ctypes.c_int32, _u32p]
         L.orc_segment_blocked.argtypes = [_f64p, _f64p, _f64p, ctypes.c_double]
         L.orc_cost_matrix.argtypes = [_f64p, ctypes.c_int32, _f64p, ctypes.c_int32,
                                       ctypes.c_double, ctypes.c_int32, _i32p]
@@ -118,6 +129,12 @@ def philox4x32_10(ctr, key) -> np.ndarray:
 
 def draw(seed: int, phase: int, iteration: int, particle: int, d: int) -> int:
     return int(lib().orc_draw(seed, phase, iteration, particle, d))
+
+
+def draws(seed: int, phase: int, iteration: int, particle: int, count: int) -> np.ndarray:
+    out = np.zeros(count, np.uint32)
+    lib().orc_draws(seed, phase, iteration, particle, count, _p(out, _u32p))
+    return out
 
 
 def segment_blocked(p, q, box, radius: float = 0.0) -> bool:

@@ -87,6 +87,14 @@ uint32_t orc_draw(uint64_t seed, uint32_t phase, uint32_t iter, uint32_t particl
     return out[draw & 3u];
 }
 
+/* Draws 0..count-1 of one (seed, phase, iteration, particle) stream. */
+void orc_draws(uint64_t seed, uint32_t phase, uint32_t iter, uint32_t particle, int32_t count,
+               uint32_t *out)
+{
+    for (int32_t d = 0; d < count; ++d)
+        out[d] = orc_draw(seed, phase, iter, particle, (uint32_t)d);
+}
+
 /* Integer in [0, m) from a 32-bit draw: multiply-shift without rejection. */
 static uint32_t bounded(uint32_t u, uint32_t m)
 {

@@ -1,0 +1,154 @@
+// Internal declarations shared by the CUDA translation units of the DPSO
+// library (enhanced discrete PSO, Phung et al., arXiv:1706.04399).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "../../include/dpso.h"
+
+namespace dpso {
+
+// Random-stream phases: the fourth counter word of every Philox draw.
+constexpr uint32_t kPhaseInit = 1;      // initial random permutations
+constexpr uint32_t kPhaseVelocity = 2;  // r1, r2 of Eq. (velocity)
+constexpr uint32_t kPhaseMutation = 3;  // Sec. 3.2.2 disturbance swaps
+
+// ---------------------------------------------------------------------------
+// Philox4x32-10 (Salmon, Moraes, Dror, Shaw, SC'11): ten rounds of two
+// 32x32->64-bit products (counter words 0 and 2 by 0xD2511F53 and 0xCD9E8D57),
+// high halves xor-ed with the other counter words and the key, the key bumped
+// by the Weyl constants 0x9E3779B9 / 0xBB67AE85 before every round but the
+// first.
+// ---------------------------------------------------------------------------
+struct Block4 {
+    uint32_t v[4];
+};
+
+__device__ __forceinline__ Block4 philox(uint32_t c0, uint32_t c1, uint32_t c2, uint32_t c3,
+                                         uint64_t seed) {
+    uint32_t k0 = static_cast<uint32_t>(seed), k1 = static_cast<uint32_t>(seed >> 32);
+#pragma unroll
+    for (int r = 0; r < 10; ++r) {
+        if (r > 0) {
+            k0 += 0x9E3779B9u;
+            k1 += 0xBB67AE85u;
+        }
+        const uint32_t lo0 = 0xD2511F53u * c0, hi0 = __umulhi(0xD2511F53u, c0);
+        const uint32_t lo1 = 0xCD9E8D57u * c2, hi1 = __umulhi(0xCD9E8D57u, c2);
+        const uint32_t n0 = hi1 ^ c1 ^ k0, n2 = hi0 ^ c3 ^ k1;
+        c0 = n0;
+        c1 = lo1;
+        c2 = n2;
+        c3 = lo0;
+    }
+    return Block4{{c0, c1, c2, c3}};
+}
+
+// Draw `d` of (seed, phase, iteration, particle): word d%4 of the block at
+// counter (d/4, particle, iteration, phase).
+__device__ __forceinline__ uint32_t draw(uint64_t seed, uint32_t phase, uint32_t iter,
+                                         uint32_t particle, uint32_t d) {
+    const Block4 b = philox(d >> 2, particle, iter, phase, seed);
+    return b.v[d & 3u];
+}
+
+// Integer in [0, m): multiply-shift of a 32-bit draw (no rejection).
+__device__ __forceinline__ uint32_t bounded(uint32_t u, uint32_t m) { return __umulhi(u, m); }
+
+// ---------------------------------------------------------------------------
+// Device control block of one swarm (one per swarm, in device memory).
+// ---------------------------------------------------------------------------
+struct Ctl {
+    long long gf;        // gbest cost
+    long long gf_start;  // gbest cost when the running generation began
+    int t;               // generations completed
+    int stall;           // consecutive generations without strict improvement
+    int done;            // stall limit reached
+    int run_two_opt;     // edge exchange scheduled in the running generation
+    int status;          // sticky device error (DPSO_OK or DPSO_ERR_*)
+    int n_det;           // particles seeded back-and-forth
+    unsigned int queue;  // 2-opt work counter
+    unsigned int pad0;
+    unsigned long long pairs;  // 2-opt candidate pairs evaluated
+    unsigned long long moves;  // 2-opt moves applied
+    unsigned long long runs;   // generations with an edge exchange
+    long long* hist;           // gbest cost after each generation
+    int hist_cap;
+    int pad1;
+};
+
+// Solver constants derived on the host from dpso_params.
+struct Consts {
+    int n, S;
+    int ldc;  // int32 row stride of the cost matrix copy
+    int ldn;  // uint16 row stride of tours / velocities
+    int flags, mut_period, mut_swaps, trigger, max_moves, stall_limit;
+    unsigned long long w_q, phi1_q, phi2_q;  // coefficients in Q32 (1.0 = 2^32)
+    unsigned long long seed;
+};
+
+// Device arrays of one swarm.
+struct SwarmDev {
+    const int* C;  // n x ldc
+    uint16_t* X;   // positions, S x ldn
+    uint16_t* V;   // velocities as label permutations, S x ldn
+    uint16_t* P;   // pbest positions, S x ldn
+    uint16_t* G;   // gbest, ldn
+    long long* F;  // fitness of X
+    long long* PF; // fitness of P
+    unsigned long long* hash;  // mutation scratch: tour hashes
+    unsigned char* dup;        // mutation scratch: duplicate flags
+    unsigned char* kept;       // mutation scratch: kept flags
+    Ctl* ctl;
+};
+
+inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
+
+// ---- launchers (cost.cu) ----
+cudaError_t launch_cost_matrix(const double* xyz, int n, const double* boxes, int m, double radius,
+                               int penalty, int* C, int ldc, int* err, cudaStream_t st);
+cudaError_t launch_check_inputs(const double* xyz, int n, const double* boxes, int m, int* err,
+                                cudaStream_t st);
+cudaError_t launch_check_cost(const int* C, int n, int ldc, int* err, cudaStream_t st);
+
+// ---- launchers (swarm.cu) ----
+cudaError_t launch_fitness(const int* C, int ldc, int n, const uint16_t* tours, int ldt, int count,
+                           long long* out, cudaStream_t st);
+cudaError_t launch_det_orders(const int* tags, int n, uint16_t* orders, int ldn, int* err,
+                              cudaStream_t st);
+cudaError_t launch_init_particles(const Consts& k, const SwarmDev& d, const uint16_t* orders,
+                                  int n_det, cudaStream_t st);
+cudaError_t launch_gbest_init(const Consts& k, const SwarmDev& d, cudaStream_t st);
+cudaError_t launch_move(const Consts& k, const SwarmDev& d, cudaStream_t st);
+cudaError_t launch_mutation(const Consts& k, const SwarmDev& d, cudaStream_t st);
+cudaError_t launch_gbest(const Consts& k, const SwarmDev& d, int second, int mut_iter,
+                         cudaStream_t st);
+cudaError_t launch_philox_draws(unsigned long long seed, uint32_t phase, uint32_t iter,
+                                uint32_t particle, int count, uint32_t* out, cudaStream_t st);
+size_t move_smem_bytes(const Consts& k, int warps);
+
+// ---- launchers (two_opt.cu) ----
+// Runs best-improvement 2-opt on `count` tours of length n (row stride ldt),
+// updating tours, costs and (when pbest != nullptr) the pbest arrays.  When
+// `gate` is non-null the kernel does nothing unless *gate != 0.  queue must
+// be zero on entry.
+struct TwoOptArgs {
+    const int* C;
+    int ldc, n;
+    uint16_t* tours;
+    int ldt, count;
+    long long* cost;
+    uint16_t* pbest;
+    long long* pcost;
+    int max_moves;
+    const int* gate;
+    unsigned int* queue;
+    unsigned long long* pairs;
+    unsigned long long* moves;
+    int* status;  // receives DPSO_ERR_INTERNAL if the move guard trips
+};
+cudaError_t launch_two_opt(const TwoOptArgs& a, int num_sms, cudaStream_t st);
+int two_opt_rows(int n);
+
+}  // namespace dpso

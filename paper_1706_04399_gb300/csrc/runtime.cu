@@ -1,0 +1,630 @@
+// Host runtime and C ABI of the DPSO library: swarm lifecycle, the generation
+// loop of Fig. "pseudocode" replayed from CUDA graphs, checkpoints, and the
+// standalone entry points (fitness, 2-opt, Philox draws, synchronous plan).
+#include <math.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <array>
+#include <vector>
+
+#include "common.cuh"
+
+using namespace dpso;
+
+namespace {
+
+#define CK(expr)                                   \
+    do {                                           \
+        if ((expr) != cudaSuccess) return DPSO_ERR_CUDA; \
+    } while (0)
+
+// Makes `dev` current for the scope of a call and restores the caller's device.
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) == cudaSuccess && prev != dev) cudaSetDevice(dev);
+        else prev = -1;
+    }
+    ~DeviceGuard() {
+        if (prev >= 0) cudaSetDevice(prev);
+    }
+};
+
+unsigned long long q32(double c) { return static_cast<unsigned long long>(llround(ldexp(c, 32))); }
+
+int validate_params(const dpso_params* p) {
+    if (!p) return DPSO_ERR_ARG;
+    auto unit = [](double v) { return isfinite(v) && v >= 0.0 && v <= 1.0; };
+    if (!unit(p->w) || !unit(p->phi1) || !unit(p->phi2)) return DPSO_ERR_ARG;
+    if (p->swarm < 1 || p->mut_period < 1 || p->mut_swaps < 0 || p->det_frac_pct < 0 ||
+        p->det_frac_pct > 100 || p->stall_limit < 0 || p->max_moves < 0 ||
+        p->two_opt_trigger < 0 || p->two_opt_trigger > 1 || (p->flags & ~7) != 0)
+        return DPSO_ERR_ARG;
+    if (p->swarm > DPSO_MAX_SWARM) return DPSO_ERR_RANGE;
+    return DPSO_OK;
+}
+
+constexpr uint32_t kStateMagic = 0x4f535044u;  // "DPSO"
+constexpr uint32_t kStateVersion = 1;
+
+struct StateHeader {
+    uint32_t magic, version;
+    int32_t n, S, t, stall, done, n_det;
+    int64_t gf;
+    uint64_t pairs, moves, runs;
+    uint64_t seed;
+    dpso_params prm;
+};
+
+}  // namespace
+
+struct dpso_swarm {
+    int device = 0, num_sms = 0;
+    dpso_params prm{};
+    Consts k{};
+    SwarmDev d{};
+    int* C = nullptr;
+    uint16_t *X = nullptr, *V = nullptr, *P = nullptr, *G = nullptr;
+    long long *F = nullptr, *PF = nullptr;
+    unsigned long long* hash = nullptr;
+    unsigned char *dup = nullptr, *kept = nullptr;
+    Ctl* ctl = nullptr;
+    long long* hist = nullptr;
+    int hist_cap = 0;
+    int n_det = 0;
+    int t_host = 0;
+    cudaStream_t last = nullptr;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t g_plain = nullptr, g_mut = nullptr;
+};
+
+namespace {
+
+void free_swarm(dpso_swarm* s) {
+    if (!s) return;
+    if (s->g_plain) cudaGraphExecDestroy(s->g_plain);
+    if (s->g_mut) cudaGraphExecDestroy(s->g_mut);
+    void* bufs[] = {s->C, s->X, s->V, s->P, s->G, s->F, s->PF, s->hash, s->dup, s->kept, s->ctl,
+                    s->hist};
+    for (void* b : bufs)
+        if (b) cudaFree(b);
+    if (s->cap) cudaStreamDestroy(s->cap);
+    delete s;
+}
+
+template <typename T>
+int dalloc(T** p, size_t count) {
+    if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return DPSO_ERR_NO_MEMORY;
+    }
+    if (cudaMemset(*p, 0, count * sizeof(T)) != cudaSuccess) return DPSO_ERR_CUDA;
+    return DPSO_OK;
+}
+
+// One generation of Fig. "pseudocode" enqueued on st: particle update, mutation
+// (when due), gbest, then the edge exchange and a second gbest pass (both
+// no-ops unless the first gbest pass scheduled the exchange).
+cudaError_t enqueue_generation(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
+    cudaError_t e = launch_move(s->k, s->d, st);
+    if (e == cudaSuccess && mut_iter) e = launch_mutation(s->k, s->d, st);
+    if (e == cudaSuccess) e = launch_gbest(s->k, s->d, 0, mut_iter ? 1 : 0, st);
+    if (e == cudaSuccess && (s->k.flags & DPSO_FLAG_TWO_OPT)) {
+        TwoOptArgs a{};
+        a.C = s->C;
+        a.ldc = s->k.ldc;
+        a.n = s->k.n;
+        a.tours = s->X;
+        a.ldt = s->k.ldn;
+        a.count = s->k.S;
+        a.cost = s->F;
+        a.pbest = s->P;
+        a.pcost = s->PF;
+        a.max_moves = s->k.max_moves;
+        a.gate = &s->ctl->run_two_opt;
+        a.queue = &s->ctl->queue;
+        a.pairs = &s->ctl->pairs;
+        a.moves = &s->ctl->moves;
+        a.status = &s->ctl->status;
+        e = launch_two_opt(a, s->num_sms, st);
+        if (e == cudaSuccess) e = launch_gbest(s->k, s->d, 1, mut_iter ? 1 : 0, st);
+    }
+    return e;
+}
+
+int capture(dpso_swarm* s, bool mut_iter, cudaGraphExec_t* out) {
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed));
+    const cudaError_t e = enqueue_generation(s, mut_iter, s->cap);
+    const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return DPSO_ERR_CUDA;
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(out, g, 0);
+    cudaGraphDestroy(g);
+    return e3 == cudaSuccess ? DPSO_OK : DPSO_ERR_CUDA;
+}
+
+// Makes room for `need` history entries (the device reads the pointer from
+// its control block, so the captured graphs stay valid).
+int ensure_history(dpso_swarm* s, int need) {
+    if (need <= s->hist_cap) return DPSO_OK;
+    int cap = std::max(1024, s->hist_cap);
+    while (cap < need) cap *= 2;
+    long long* nh = nullptr;
+    int st = dalloc(&nh, static_cast<size_t>(cap));
+    if (st) return st;
+    CK(cudaStreamSynchronize(s->last));
+    if (s->hist_cap > 0)
+        CK(cudaMemcpy(nh, s->hist, sizeof(long long) * s->hist_cap, cudaMemcpyDeviceToDevice));
+    CK(cudaMemcpy(&s->ctl->hist, &nh, sizeof(nh), cudaMemcpyHostToDevice));
+    CK(cudaMemcpy(&s->ctl->hist_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice));
+    cudaFree(s->hist);
+    s->hist = nh;
+    s->hist_cap = cap;
+    return DPSO_OK;
+}
+
+int read_ctl(dpso_swarm* s, Ctl* c) {
+    CK(cudaStreamSynchronize(s->last));
+    CK(cudaMemcpy(c, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    return DPSO_OK;
+}
+
+__global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err) {
+    extern __shared__ unsigned char seen[];
+    const uint16_t* x = tours + static_cast<size_t>(blockIdx.x) * n;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) seen[i] = 0;
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int v = x[i];
+        if (v >= n) atomicOr(err, 1);
+        else seen[v] = 1;
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x)
+        if (!seen[i]) atomicOr(err, 1);
+}
+
+}  // namespace
+
+extern "C" {
+
+void dpso_default_params(dpso_params* p) {
+    if (!p) return;
+    p->w = 1.0;
+    p->phi1 = 0.4;
+    p->phi2 = 0.4;
+    p->swarm = 100;
+    p->mut_period = 3;
+    p->mut_swaps = 2;
+    p->det_frac_pct = 10;
+    p->stall_limit = 0;
+    p->flags = DPSO_FLAG_DET_INIT | DPSO_FLAG_MUTATION | DPSO_FLAG_TWO_OPT;
+    p->two_opt_trigger = 0;
+    p->max_moves = 0;
+}
+
+void dpso_default_cost_params(dpso_cost_params* p) {
+    if (!p) return;
+    p->uav_radius_m = 0.0;
+    p->blocked_penalty_mm = 1000000;
+    p->reserved = 0;
+}
+
+const char* dpso_status_string(int status) {
+    switch (status) {
+        case DPSO_OK: return "ok";
+        case DPSO_ERR_ARG: return "invalid argument";
+        case DPSO_ERR_RANGE: return "value out of range";
+        case DPSO_ERR_NO_MEMORY: return "out of device memory";
+        case DPSO_ERR_CUDA: return "CUDA runtime error";
+        case DPSO_ERR_TIMEOUT: return "device wait timed out";
+        case DPSO_ERR_INTERNAL: return "internal error";
+        default: return "unknown status";
+    }
+}
+
+int dpso_fitness(const int32_t* C_dev, int32_t n, const uint16_t* tours_dev, int32_t count,
+                 int64_t* cost_dev, void* stream) {
+    if (!C_dev || !tours_dev || !cost_dev || n < 1 || count < 0) return DPSO_ERR_ARG;
+    if (n > DPSO_MAX_N) return DPSO_ERR_RANGE;
+    CK(launch_fitness(C_dev, n, n, tours_dev, n, count, reinterpret_cast<long long*>(cost_dev),
+                      static_cast<cudaStream_t>(stream)));
+    return DPSO_OK;
+}
+
+int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t count,
+                 int64_t* cost_dev, int32_t max_moves, int64_t* pairs_host, int64_t* moves_host,
+                 void* stream) {
+    if (!C_dev || !tours_dev || !cost_dev || n < 3 || count < 0 || max_moves < 0)
+        return DPSO_ERR_ARG;
+    if (n > DPSO_MAX_N) return DPSO_ERR_RANGE;
+    if (pairs_host) *pairs_host = 0;
+    if (moves_host) *moves_host = 0;
+    if (count == 0) return DPSO_OK;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    int dev = 0, sms = 0;
+    CK(cudaGetDevice(&dev));
+    CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    // scratch: [0] error word, [1] queue, [2..3] pairs, [4..5] moves
+    unsigned int* scratch = nullptr;
+    if (cudaMallocAsync(&scratch, 8 * sizeof(unsigned int), st) != cudaSuccess) {
+        cudaGetLastError();
+        return DPSO_ERR_NO_MEMORY;
+    }
+    int* err = reinterpret_cast<int*>(scratch);
+    int herr = 0;
+    unsigned long long counters[2] = {0, 0};
+    cudaError_t e = cudaMemsetAsync(scratch, 0, 8 * sizeof(unsigned int), st);
+    if (e == cudaSuccess) e = launch_check_cost(C_dev, n, n, err, st);
+    if (e == cudaSuccess) {
+        tours_valid_kernel<<<count, 256, n, st>>>(tours_dev, n, err);
+        e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaSuccess && herr == 0) {
+        e = launch_fitness(C_dev, n, n, tours_dev, n, count, reinterpret_cast<long long*>(cost_dev),
+                           st);
+        TwoOptArgs a{};
+        a.C = C_dev;
+        a.ldc = n;
+        a.n = n;
+        a.tours = tours_dev;
+        a.ldt = n;
+        a.count = count;
+        a.cost = reinterpret_cast<long long*>(cost_dev);
+        a.max_moves = max_moves;
+        a.queue = scratch + 1;
+        a.pairs = reinterpret_cast<unsigned long long*>(scratch + 2);
+        a.moves = reinterpret_cast<unsigned long long*>(scratch + 4);
+        a.status = err;
+        if (e == cudaSuccess) e = launch_two_opt(a, sms, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(counters, scratch + 2, sizeof(counters), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+    }
+    cudaFreeAsync(scratch, st);
+    if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e != cudaSuccess) return DPSO_ERR_CUDA;
+    if (herr == DPSO_ERR_INTERNAL) return DPSO_ERR_INTERNAL;
+    if (herr & 1) return DPSO_ERR_ARG;
+    if (herr & 2) return DPSO_ERR_RANGE;
+    if (pairs_host) *pairs_host = static_cast<int64_t>(counters[0]);
+    if (moves_host) *moves_host = static_cast<int64_t>(counters[1]);
+    return DPSO_OK;
+}
+
+int dpso_philox_draws(uint64_t seed, uint32_t phase, uint32_t iteration, uint32_t particle,
+                      int32_t count, uint32_t* out_dev, void* stream) {
+    if (count < 0 || (count > 0 && !out_dev)) return DPSO_ERR_ARG;
+    CK(launch_philox_draws(seed, phase, iteration, particle, count, out_dev,
+                           static_cast<cudaStream_t>(stream)));
+    return DPSO_OK;
+}
+
+int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* tags_host,
+              const dpso_params* p, uint64_t seed, void* stream) {
+    if (!out || !C_dev) return DPSO_ERR_ARG;
+    *out = nullptr;
+    int st = validate_params(p);
+    if (st) return st;
+    if (n < 3) return DPSO_ERR_ARG;
+    if (n > DPSO_MAX_N) return DPSO_ERR_RANGE;
+    const bool det = (p->flags & DPSO_FLAG_DET_INIT) && tags_host;
+    if (det) {
+        std::vector<std::array<int, 3>> tg(n);
+        for (int i = 0; i < n; ++i) {
+            for (int a = 0; a < 3; ++a) {
+                tg[i][a] = tags_host[3 * i + a];
+                if (tg[i][a] < 0) return DPSO_ERR_ARG;
+            }
+        }
+        std::sort(tg.begin(), tg.end());
+        for (int i = 1; i < n; ++i)
+            if (tg[i] == tg[i - 1]) return DPSO_ERR_ARG;
+    }
+
+    dpso_swarm* s = new dpso_swarm();
+    cudaStream_t ust = static_cast<cudaStream_t>(stream);
+    s->last = ust;
+    s->prm = *p;
+    auto fail = [&](int code) {
+        free_swarm(s);
+        return code;
+    };
+    if (cudaGetDevice(&s->device) != cudaSuccess) return fail(DPSO_ERR_CUDA);
+    if (cudaDeviceGetAttribute(&s->num_sms, cudaDevAttrMultiProcessorCount, s->device) !=
+        cudaSuccess)
+        return fail(DPSO_ERR_CUDA);
+    if (two_opt_rows(n) == 0) return fail(DPSO_ERR_RANGE);
+
+    Consts& k = s->k;
+    k.n = n;
+    k.S = p->swarm;
+    k.ldc = round_up(n, 32);
+    k.ldn = round_up(n, 8);
+    k.flags = p->flags;
+    k.mut_period = p->mut_period;
+    k.mut_swaps = p->mut_swaps;
+    k.trigger = p->two_opt_trigger;
+    k.max_moves = p->max_moves;
+    k.stall_limit = p->stall_limit;
+    k.w_q = q32(p->w);
+    k.phi1_q = q32(p->phi1);
+    k.phi2_q = q32(p->phi2);
+    k.seed = seed;
+    const size_t S = static_cast<size_t>(k.S), ldn = static_cast<size_t>(k.ldn);
+
+    if ((st = dalloc(&s->C, static_cast<size_t>(n) * k.ldc)) || (st = dalloc(&s->X, S * ldn)) ||
+        (st = dalloc(&s->V, S * ldn)) || (st = dalloc(&s->P, S * ldn)) ||
+        (st = dalloc(&s->G, ldn)) || (st = dalloc(&s->F, S)) || (st = dalloc(&s->PF, S)) ||
+        (st = dalloc(&s->hash, S)) || (st = dalloc(&s->dup, S)) || (st = dalloc(&s->kept, S)) ||
+        (st = dalloc(&s->ctl, 1)))
+        return fail(st);
+    if ((st = ensure_history(s, 1024))) return fail(st);
+    // the zero-fills above ran on the legacy stream; the caller's stream may
+    // be non-blocking, so finish them before enqueuing on it
+    if (cudaDeviceSynchronize() != cudaSuccess) return fail(DPSO_ERR_CUDA);
+    s->d = SwarmDev{s->C, s->X, s->V, s->P, s->G, s->F, s->PF, s->hash, s->dup, s->kept, s->ctl};
+
+    int* err = nullptr;
+    uint16_t* orders = nullptr;
+    int* tags_dev = nullptr;
+    if ((st = dalloc(&err, 1))) return fail(st);
+    auto fail2 = [&](int code) {
+        cudaFree(err);
+        cudaFree(orders);
+        cudaFree(tags_dev);
+        return fail(code);
+    };
+    if (cudaMemcpy2DAsync(s->C, sizeof(int) * k.ldc, C_dev, sizeof(int) * n, sizeof(int) * n, n,
+                          cudaMemcpyDeviceToDevice, ust) != cudaSuccess ||
+        launch_check_cost(s->C, n, k.ldc, err, ust) != cudaSuccess)
+        return fail2(DPSO_ERR_CUDA);
+    if (det) {
+        s->n_det = static_cast<int>((static_cast<long long>(k.S) * p->det_frac_pct) / 100);
+        s->n_det = std::min(k.S, std::max(1, s->n_det));
+        if ((st = dalloc(&orders, 8 * ldn)) || (st = dalloc(&tags_dev, 3 * static_cast<size_t>(n))))
+            return fail2(st);
+        if (cudaMemcpyAsync(tags_dev, tags_host, sizeof(int) * 3 * n, cudaMemcpyHostToDevice, ust) !=
+                cudaSuccess ||
+            launch_det_orders(tags_dev, n, orders, k.ldn, err, ust) != cudaSuccess)
+            return fail2(DPSO_ERR_CUDA);
+    }
+    int herr = 0;
+    if (cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, ust) != cudaSuccess ||
+        cudaStreamSynchronize(ust) != cudaSuccess)
+        return fail2(DPSO_ERR_CUDA);
+    if (herr & 1) return fail2(DPSO_ERR_ARG);
+    if (herr & 2) return fail2(DPSO_ERR_RANGE);
+
+    if (launch_init_particles(k, s->d, orders, s->n_det, ust) != cudaSuccess ||
+        launch_fitness(s->C, k.ldc, n, s->X, k.ldn, k.S, s->F, ust) != cudaSuccess ||
+        cudaMemcpyAsync(s->PF, s->F, sizeof(long long) * S, cudaMemcpyDeviceToDevice, ust) !=
+            cudaSuccess ||
+        launch_gbest_init(k, s->d, ust) != cudaSuccess ||
+        cudaMemcpyAsync(&s->ctl->n_det, &s->n_det, sizeof(int), cudaMemcpyHostToDevice, ust) !=
+            cudaSuccess ||
+        cudaStreamSynchronize(ust) != cudaSuccess)
+        return fail2(DPSO_ERR_CUDA);
+    cudaFree(err);
+    cudaFree(orders);
+    cudaFree(tags_dev);
+
+    if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(DPSO_ERR_CUDA);
+    if ((st = capture(s, false, &s->g_plain)) || (st = capture(s, true, &s->g_mut))) return fail(st);
+    *out = s;
+    return DPSO_OK;
+}
+
+int dpso_step(dpso_swarm* s, int32_t iterations, void* stream) {
+    if (!s || iterations < 0) return DPSO_ERR_ARG;
+    if (iterations == 0) return DPSO_OK;
+    DeviceGuard g(s->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    if (st != s->last) {
+        // order this call after everything already enqueued on the previous stream
+        CK(cudaStreamSynchronize(s->last));
+        s->last = st;
+    }
+    const int st2 = ensure_history(s, s->t_host + iterations);
+    if (st2) return st2;
+    for (int it = 0; it < iterations; ++it) {
+        const int t = s->t_host + 1 + it;
+        const bool mut = (s->k.flags & DPSO_FLAG_MUTATION) && (t % s->k.mut_period == 0);
+        CK(cudaGraphLaunch(mut ? s->g_mut : s->g_plain, st));
+    }
+    s->t_host += iterations;
+    return DPSO_OK;
+}
+
+int dpso_get_best(dpso_swarm* s, int32_t* tour_host, int64_t* cost) {
+    if (!s || !tour_host || !cost) return DPSO_ERR_ARG;
+    DeviceGuard g(s->device);
+    Ctl c;
+    const int st = read_ctl(s, &c);
+    if (st) return st;
+    std::vector<uint16_t> tmp(s->k.n);
+    CK(cudaMemcpy(tmp.data(), s->G, sizeof(uint16_t) * s->k.n, cudaMemcpyDeviceToHost));
+    for (int i = 0; i < s->k.n; ++i) tour_host[i] = tmp[i];
+    *cost = c.gf;
+    return c.status ? c.status : DPSO_OK;
+}
+
+int dpso_get_history(dpso_swarm* s, int64_t* gbest_host, int32_t cap, int32_t* len) {
+    if (!s || !len || cap < 0 || (cap > 0 && !gbest_host)) return DPSO_ERR_ARG;
+    DeviceGuard g(s->device);
+    Ctl c;
+    const int st = read_ctl(s, &c);
+    if (st) return st;
+    *len = c.t;
+    const int k = std::min(cap, c.t);
+    if (k > 0) CK(cudaMemcpy(gbest_host, s->hist, sizeof(int64_t) * k, cudaMemcpyDeviceToHost));
+    return DPSO_OK;
+}
+
+int dpso_get_stats(dpso_swarm* s, dpso_stats* out) {
+    if (!s || !out) return DPSO_ERR_ARG;
+    DeviceGuard g(s->device);
+    Ctl c;
+    const int st = read_ctl(s, &c);
+    if (st) return st;
+    memset(out, 0, sizeof(*out));
+    out->iterations = c.t;
+    out->stalled = c.done;
+    out->gbest_cost = c.gf;
+    out->two_opt_pairs = static_cast<int64_t>(c.pairs);
+    out->two_opt_moves = static_cast<int64_t>(c.moves);
+    out->two_opt_runs = static_cast<int64_t>(c.runs);
+    out->device_status = c.status;
+    return DPSO_OK;
+}
+
+int dpso_get_state(dpso_swarm* s, void* buf, size_t* bytes) {
+    if (!s || !bytes) return DPSO_ERR_ARG;
+    DeviceGuard g(s->device);
+    Ctl c;
+    int st = read_ctl(s, &c);
+    if (st) return st;
+    const size_t n = s->k.n, S = s->k.S;
+    const size_t need = sizeof(StateHeader) + 3 * S * n * sizeof(uint16_t) + n * sizeof(uint16_t) +
+                        2 * S * sizeof(int64_t) + static_cast<size_t>(c.t) * sizeof(int64_t);
+    if (!buf) {
+        *bytes = need;
+        return DPSO_OK;
+    }
+    if (*bytes < need) return DPSO_ERR_ARG;
+    unsigned char* o = static_cast<unsigned char*>(buf);
+    StateHeader h{};
+    h.magic = kStateMagic;
+    h.version = kStateVersion;
+    h.n = s->k.n;
+    h.S = s->k.S;
+    h.t = c.t;
+    h.stall = c.stall;
+    h.done = c.done;
+    h.n_det = c.n_det;
+    h.gf = c.gf;
+    h.pairs = c.pairs;
+    h.moves = c.moves;
+    h.runs = c.runs;
+    h.seed = s->k.seed;
+    h.prm = s->prm;
+    memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    const size_t row = n * sizeof(uint16_t), pitch = s->k.ldn * sizeof(uint16_t);
+    for (uint16_t* A : {s->X, s->V, s->P}) {
+        CK(cudaMemcpy2D(o, row, A, pitch, row, S, cudaMemcpyDeviceToHost));
+        o += row * S;
+    }
+    CK(cudaMemcpy(o, s->G, row, cudaMemcpyDeviceToHost));
+    o += row;
+    CK(cudaMemcpy(o, s->F, S * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    o += S * sizeof(int64_t);
+    CK(cudaMemcpy(o, s->PF, S * sizeof(int64_t), cudaMemcpyDeviceToHost));
+    o += S * sizeof(int64_t);
+    if (c.t > 0) CK(cudaMemcpy(o, s->hist, sizeof(int64_t) * c.t, cudaMemcpyDeviceToHost));
+    *bytes = need;
+    return DPSO_OK;
+}
+
+int dpso_set_state(dpso_swarm* s, const void* buf, size_t bytes) {
+    if (!s || !buf || bytes < sizeof(StateHeader)) return DPSO_ERR_ARG;
+    DeviceGuard g(s->device);
+    StateHeader h;
+    memcpy(&h, buf, sizeof(h));
+    if (h.magic != kStateMagic || h.version != kStateVersion || h.n != s->k.n || h.S != s->k.S ||
+        h.seed != s->k.seed || memcmp(&h.prm, &s->prm, sizeof(dpso_params)) != 0 || h.t < 0)
+        return DPSO_ERR_ARG;
+    const size_t n = s->k.n, S = s->k.S;
+    const size_t need = sizeof(StateHeader) + 3 * S * n * sizeof(uint16_t) + n * sizeof(uint16_t) +
+                        2 * S * sizeof(int64_t) + static_cast<size_t>(h.t) * sizeof(int64_t);
+    if (bytes < need) return DPSO_ERR_ARG;
+    CK(cudaStreamSynchronize(s->last));
+    int st = ensure_history(s, std::max(h.t, 1));
+    if (st) return st;
+    const unsigned char* o = static_cast<const unsigned char*>(buf) + sizeof(h);
+    const size_t row = n * sizeof(uint16_t), pitch = s->k.ldn * sizeof(uint16_t);
+    for (uint16_t* A : {s->X, s->V, s->P}) {
+        CK(cudaMemcpy2D(A, pitch, o, row, row, S, cudaMemcpyHostToDevice));
+        o += row * S;
+    }
+    CK(cudaMemcpy(s->G, o, row, cudaMemcpyHostToDevice));
+    o += row;
+    CK(cudaMemcpy(s->F, o, S * sizeof(int64_t), cudaMemcpyHostToDevice));
+    o += S * sizeof(int64_t);
+    CK(cudaMemcpy(s->PF, o, S * sizeof(int64_t), cudaMemcpyHostToDevice));
+    o += S * sizeof(int64_t);
+    if (h.t > 0) CK(cudaMemcpy(s->hist, o, sizeof(int64_t) * h.t, cudaMemcpyHostToDevice));
+    Ctl c;
+    CK(cudaMemcpy(&c, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    c.gf = h.gf;
+    c.gf_start = h.gf;
+    c.t = h.t;
+    c.stall = h.stall;
+    c.done = h.done;
+    c.run_two_opt = 0;
+    c.status = DPSO_OK;
+    c.n_det = h.n_det;
+    c.queue = 0;
+    c.pairs = h.pairs;
+    c.moves = h.moves;
+    c.runs = h.runs;
+    CK(cudaMemcpy(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+    s->t_host = h.t;
+    return DPSO_OK;
+}
+
+void dpso_destroy(dpso_swarm* s) {
+    if (!s) return;
+    DeviceGuard g(s->device);
+    cudaStreamSynchronize(s->last);
+    free_swarm(s);
+}
+
+int dpso_plan(const double* xyz_host, int32_t n, const double* boxes_host, int32_t m,
+              const int32_t* tags_host, const dpso_cost_params* cp, const dpso_params* p,
+              uint64_t seed, int32_t iterations, int32_t* tour_host, int64_t* cost) {
+    if (!xyz_host || !cp || !p || !tour_host || !cost || n < 3 || m < 0 || iterations < 0 ||
+        (m > 0 && !boxes_host))
+        return DPSO_ERR_ARG;
+    if (n > DPSO_MAX_N) return DPSO_ERR_RANGE;
+    int st = validate_params(p);
+    if (st) return st;
+    cudaStream_t s = nullptr;
+    CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+    double *xyz = nullptr, *boxes = nullptr;
+    int* C = nullptr;
+    dpso_swarm* sw = nullptr;
+    st = DPSO_OK;
+    if (cudaMalloc(&xyz, sizeof(double) * 3 * n) != cudaSuccess ||
+        cudaMalloc(&boxes, sizeof(double) * 6 * std::max(m, 1)) != cudaSuccess ||
+        cudaMalloc(&C, sizeof(int) * static_cast<size_t>(n) * n) != cudaSuccess) {
+        cudaGetLastError();
+        st = DPSO_ERR_NO_MEMORY;
+    }
+    if (!st && (cudaMemcpyAsync(xyz, xyz_host, sizeof(double) * 3 * n, cudaMemcpyHostToDevice, s) !=
+                    cudaSuccess ||
+                (m > 0 && cudaMemcpyAsync(boxes, boxes_host, sizeof(double) * 6 * m,
+                                          cudaMemcpyHostToDevice, s) != cudaSuccess)))
+        st = DPSO_ERR_CUDA;
+    if (!st) st = dpso_cost_matrix(xyz, n, boxes, m, cp, C, s);
+    if (!st) st = dpso_init(&sw, C, n, tags_host, p, seed, s);
+    if (!st) st = dpso_step(sw, iterations, s);
+    if (!st) st = dpso_get_best(sw, tour_host, cost);
+    if (sw) dpso_destroy(sw);
+    cudaFree(xyz);
+    cudaFree(boxes);
+    cudaFree(C);
+    cudaStreamDestroy(s);
+    return st;
+}
+
+}  // extern "C"

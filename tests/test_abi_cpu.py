@@ -1,0 +1,59 @@
+"""Host-side checks of the C-ABI library that need no GPU: it builds for
+sm_103a, loads, and exports every function include/dpso.h declares."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from conftest import ROOT
+
+
+def _declared_functions():
+    src = open(os.path.join(ROOT, "include", "dpso.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    return sorted(set(re.findall(r"\b(dpso_\w+)\s*\(", src)))
+
+
+@pytest.fixture(scope="module")
+def libpath():
+    from paper_1706_04399_gb300 import build
+    return build.build()
+
+
+def test_header_declares_the_boundary():
+    names = _declared_functions()
+    for required in ("dpso_cost_matrix", "dpso_init", "dpso_step", "dpso_plan"):
+        assert required in names
+
+
+def test_library_exports_every_declared_symbol(libpath):
+    lib = ctypes.CDLL(libpath)
+    missing = [n for n in _declared_functions() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_only_entry_points(libpath):
+    from paper_1706_04399_gb300 import dpso
+    p = dpso.default_params()
+    assert (p.w, p.phi1, p.phi2, p.mut_period, p.det_frac_pct) == (1.0, 0.4, 0.4, 3, 10)
+    assert p.flags == dpso.FLAGS_ALL
+    assert dpso.default_cost_params().blocked_penalty_mm == 1_000_000
+    assert dpso.status_string(dpso.ERR_RANGE) == "value out of range"
+
+
+def test_argument_errors_need_no_device(libpath):
+    from paper_1706_04399_gb300 import dpso
+    L = dpso.lib()
+    # rejected before any CUDA call
+    assert L.dpso_cost_matrix(None, 10, None, 0, ctypes.byref(dpso.default_cost_params()),
+                              None, None) == dpso.ERR_ARG
+    assert L.dpso_step(None, 1, None) == dpso.ERR_ARG
+    bad = dpso.default_params(swarm=0)
+    h = ctypes.c_void_p()
+    assert L.dpso_init(ctypes.byref(h), 1, 10, None, ctypes.byref(bad), 1, None) == dpso.ERR_ARG
+    big = dpso.default_params(swarm=70000)
+    assert L.dpso_init(ctypes.byref(h), 1, 10, None, ctypes.byref(big), 1, None) == dpso.ERR_RANGE
+    ok = dpso.default_params()
+    assert L.dpso_init(ctypes.byref(h), 1, dpso.MAX_N + 1, None, ctypes.byref(ok), 1,
+                       None) == dpso.ERR_RANGE

@@ -1,0 +1,391 @@
+#!/usr/bin/env python
+"""Throughput benchmark of the GB300 DPSO hot path.
+
+Workload: the office-facade-shaped instance (400 viewpoints on a 20x20 grid
+over a 40 m x 30 m wall, 3 m stand-off, +-0.2 m jitter, 5 random boxes),
+swarm 1024, the paper's w = 1, phi1 = phi2 = 0.4, mutation every third
+generation, back-and-forth seeding and edge exchange on.  A step is one DPSO
+generation (Fig. "pseudocode"): particle update + fitness + pbest, mutation
+when due, gbest, and the edge exchange whenever the gbest did not improve.
+
+value   particle-iterations/s = particles x generations / device time, with the
+        cost matrix and swarm resident in HBM; the L2 is flushed between timed
+        generations.  For N > 1 each rank runs an independent replica (the
+        solver has no exchange step to shard).
+e2e     the same metric through dpso_plan from pinned host buffers: copies in,
+        cost matrix, initialisation, `steps` generations, best tour out.
+roofline  the 2-opt kernel: 8 bytes of C per candidate pair (two int32 entries)
+        over its CUDA-event time, against the L2 bandwidth measured in this run.
+
+`--impl reference` times the CPU oracle on a bounded sample of the workload.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "DPSO particle-iterations/s and 2-opt moves/s per GB300; batched p99 latency"
+UNIT = "particle-iterations/s"
+BYTES_PER_PAIR = 8          # C[x_i][x_j] + C[x_i+1][x_j+1], int32 each
+CPU_SAMPLE_SWARM = 16       # oracle sample: particles
+CPU_SAMPLE_GENERATIONS = 10 # oracle sample: generations
+
+
+def _env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+def workload(name: str):
+    from paper_1706_04399_gb300 import inputs
+    return inputs.CONFIGS[name]()
+
+
+def cpu_cores() -> int:
+    try:
+        return len(os.sched_getaffinity(0))
+    except AttributeError:
+        return os.cpu_count() or 1
+
+
+def cpu_model() -> str:
+    try:
+        with open("/proc/cpuinfo") as fh:
+            for line in fh:
+                if line.lower().startswith(("model name", "cpu part")):
+                    return line.split(":", 1)[1].strip()
+    except OSError:
+        pass
+    return "unknown"
+
+
+# ----------------------------------------------------------------- CPU oracle
+
+def oracle_sample(inst, swarm: int, warmup: int, generations: int):
+    """Times the oracle (single thread) on `generations` generations of a
+    `swarm`-particle swarm over the same instance; returns (value, seconds)."""
+    import oracle
+    C, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
+    sw = oracle.Swarm(C, inst.tags, swarm=swarm, seed=inst.seed)
+    if warmup:
+        sw.run(warmup)
+    t0 = time.perf_counter()
+    sw.run(generations)
+    dt = time.perf_counter() - t0
+    return swarm * generations / dt, dt
+
+
+def run_reference(args):
+    rank = _env_int("RANK", 0)
+    if rank != 0:
+        return 0
+    inst = workload(args.workload)
+    per_step = []
+    import oracle
+    C, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
+    sw = oracle.Swarm(C, inst.tags, swarm=CPU_SAMPLE_SWARM, seed=inst.seed)
+    sw.run(args.warmup)
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        sw.iterate()
+        per_step.append(time.perf_counter() - t0)
+    total = sum(per_step)
+    value = CPU_SAMPLE_SWARM * args.steps / total
+    sample = (f"{inst.name} instance (n={inst.n}), oracle swarm of {CPU_SAMPLE_SWARM} particles "
+              f"instead of {inst.swarm}, {args.warmup} untimed + {args.steps} timed generations")
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": f"{inst.name}-{inst.n}vp", "n": inst.n, "swarm": inst.swarm},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": sample, "cpu": cpu_model()},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line))
+    return 0
+
+
+# ------------------------------------------------------------------ GPU helpers
+
+class ClockSampler:
+    """nvidia-smi clock / throttle samples every 200 ms while running."""
+
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+              "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+              "clocks_event_reasons.sw_power_cap,utilization.gpu")
+
+    def __init__(self, index: str | None):
+        self.index = index
+        self.proc = None
+        self.out = os.path.join("/tmp", f"dpso_clocks_{os.getpid()}.csv")
+
+    def __enter__(self):
+        cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+               "-lms", "200"]
+        if self.index is not None:
+            cmd += ["-i", self.index]
+        try:
+            self.fh = open(self.out, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not os.path.exists(self.out):
+            return None
+        rows = []
+        with open(self.out) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.out)
+        if not rows:
+            return None
+
+        def num(v):
+            try:
+                return float(v)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        util = [num(r[7]) for r in rows]
+        loaded = [num(r[0]) for r in rows if num(r[7]) is not None and num(r[7]) > 50
+                  and num(r[0]) is not None] or sm
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[3 + k] == "Active"})
+        return {"sm_mhz": statistics.median(loaded) if loaded else None,
+                "sm_max_mhz": max(num(r[1]) or 0 for r in rows),
+                "reasons": reasons, "samples": len(rows),
+                "samples_under_load": sum(1 for u in util if u is not None and u > 50)}
+
+
+def gpu_index_for_smi(local_rank: int) -> str | None:
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+    if vis:
+        ids = [v for v in vis.split(",") if v.strip()]
+        if local_rank < len(ids):
+            return ids[local_rank].strip()
+    return str(local_rank)
+
+
+def l2_copy_gbs(torch) -> float:
+    """L2 bandwidth: best copy_ rate between two L2-resident 24 MiB buffers."""
+    n = 24 << 20
+    a = torch.ones(n, dtype=torch.uint8, device="cuda")
+    b = torch.empty_like(a)
+    for _ in range(5):
+        b.copy_(a)
+    best = float("inf")
+    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(20):
+        s.record()
+        for _ in range(10):
+            b.copy_(a)
+        e.record()
+        e.synchronize()
+        best = min(best, s.elapsed_time(e) / 10)
+    return 2 * n / (best * 1e-3) / 1e9
+
+
+def measured_peaks() -> dict:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh)
+    except (OSError, ValueError):
+        return {}
+
+
+def two_opt_traffic(workload_name: str):
+    """DRAM bytes per 2-opt launch from the committed ncu summary, if it was
+    taken from the current kernel source (else None)."""
+    src = os.path.join(ROOT, "paper_1706_04399_gb300", "csrc", "two_opt.cu")
+    path = os.path.join(ROOT, "profiles", "two_opt_dram_traffic.json")
+    try:
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        rec = json.load(open(path))
+    except (OSError, ValueError):
+        return None
+    if rec.get("kernel_source_sha256") != digest or rec.get("workload") != workload_name:
+        return None
+    return rec.get("dram_bytes_per_launch")
+
+
+def gpu_line(args):
+    import numpy as np
+    import torch
+
+    from paper_1706_04399_gb300 import dpso
+
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+
+    inst = workload(args.workload)
+    seed = inst.seed + rank        # independent replica per rank
+    S, n = inst.swarm, inst.n
+    stream = torch.cuda.current_stream()
+
+    xyz = torch.from_numpy(inst.xyz).cuda()
+    boxes = torch.from_numpy(inst.boxes).cuda()
+    C = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    dpso.dpso_cost_matrix(xyz, n, boxes, inst.m, dpso.default_cost_params(), C, stream)
+    params = dpso.default_params(swarm=S)
+    sw = dpso.Swarm(C, n, inst.tags, params, seed, stream)
+    sw.set_timing(True)
+    sw.step(args.warmup, stream)
+    torch.cuda.synchronize()
+    sw.set_timing(True)            # clears the accumulators: only timed steps count
+    st0 = sw.stats()
+
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    sampler = ClockSampler(gpu_index_for_smi(local))
+    wall0 = time.perf_counter()
+    with sampler:
+        for k in range(args.steps):
+            flush.zero_()                      # evict the L2 between generations
+            evs[k][0].record(stream)
+            sw.step(1, stream)
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    if dist:
+        dist.barrier()
+    dev_ms = sum(a.elapsed_time(b) for a, b in evs)
+    timing = sw.timing()
+    st1 = sw.stats()
+    if dist:
+        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        dev_ms_max = float(t.item())
+    else:
+        dev_ms_max = dev_ms
+    units = world * S * args.steps
+    value = units / (dev_ms_max / 1e3)
+
+    pairs = st1["two_opt_pairs"] - st0["two_opt_pairs"]
+    moves = st1["two_opt_moves"] - st0["two_opt_moves"]
+    two_ms = timing["ms"]["two_opt"]
+    launches = sum(timing["launches"].values())
+    out = None
+    if rank == 0:
+        peaks = measured_peaks()
+        l2 = l2_copy_gbs(torch)
+        achieved = BYTES_PER_PAIR * pairs / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
+        traffic = two_opt_traffic(inst.name)
+        roofline = {
+            "kernel": "two_opt_kernel", "bound": "l2", "achieved": achieved, "peak": l2,
+            "unit": "GB/s", "frac": achieved / l2 if l2 else None,
+            "traffic": traffic,
+            "peak_source": "L2 copy bandwidth measured in this run (24 MiB buffers)",
+            "hbm_peak_gbs": peaks.get("hbm_gbs"),
+            "frac_of_hbm_peak": achieved / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
+        }
+        cpu = None
+        if world == 1 and not args.no_cpu_baseline:
+            cval, csec = oracle_sample(inst, CPU_SAMPLE_SWARM, 0, CPU_SAMPLE_GENERATIONS)
+            cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
+                   "sample": f"{inst.name} instance (n={n}), oracle swarm of {CPU_SAMPLE_SWARM} "
+                             f"particles, first {CPU_SAMPLE_GENERATIONS} generations "
+                             f"({csec:.1f} s)",
+                   "host_cores": cpu_cores(), "cpu": cpu_model()}
+        e2e = None
+        if not args.no_e2e:
+            pin = lambda a: torch.from_numpy(np.ascontiguousarray(a)).pin_memory()  # noqa: E731
+            hx, hb, ht = pin(inst.xyz), pin(inst.boxes), pin(inst.tags)
+            tour = torch.empty(n, dtype=torch.int32).pin_memory()
+            import ctypes
+            cost = ctypes.c_int64(0)
+            cp = dpso.default_cost_params()
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            rc = dpso.lib().dpso_plan(hx.data_ptr(), n, hb.data_ptr(), inst.m, ht.data_ptr(),
+                                      ctypes.byref(cp), ctypes.byref(params), seed, args.steps,
+                                      ctypes.cast(tour.data_ptr(), ctypes.POINTER(ctypes.c_int32)),
+                                      ctypes.byref(cost))
+            e2e_s = time.perf_counter() - t0
+            if rc != 0:
+                raise dpso.DpsoError(rc, "dpso_plan")
+            e2e = {"value": S * args.steps / e2e_s, "unit": UNIT,
+                   "h2d_bytes_per_step": int(hx.numel() * 8 + hb.numel() * 8 + ht.numel() * 4),
+                   "d2h_bytes_per_step": int(n * 4 + 8),
+                   "what": f"dpso_plan: {args.steps} generations from host buffers, including "
+                           "cost matrix and initialisation"}
+        phases = {k: round(v, 3) for k, v in timing["ms"].items()}
+        out = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+            "config": {"workload": f"{inst.name}-{n}vp-{S}p", "n": n, "swarm": S,
+                       "generations_timed": args.steps, "boxes": inst.m,
+                       "l2": "flushed between timed generations (256 MiB write)",
+                       "parallelism": "replicas" if world > 1 else "single"},
+            "two_opt_pairs_per_s": pairs / (two_ms / 1e3) if two_ms > 0 else 0.0,
+            "two_opt_moves_applied": moves, "two_opt_pairs": pairs,
+            "phase_ms": phases, "wall_s": wall,
+            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "gpu_launches": launches, "clocks": sampler.summary(),
+            "gbest_cost_mm": st1["gbest_cost"],
+        }
+    sw.close()
+    if dist:
+        dist.destroy_process_group()
+    return out
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=30)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--workload", default="facade", choices=["tiny", "facade", "bridge"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    args = ap.parse_args(argv)
+    if args.warmup < 3 and args.impl == "gb300":
+        print("note: fewer than 3 warm-up steps", file=sys.stderr)
+    if args.impl == "reference":
+        return run_reference(args)
+    out = gpu_line(args)
+    if out is not None:
+        print(json.dumps(out))
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -99,6 +99,21 @@ typedef struct dpso_stats {
     int32_t reserved;
 } dpso_stats;
 
+/* Per-phase device time of a swarm's generations while timing is on
+ * (dpso_set_timing), accumulated from CUDA events recorded on the stream the
+ * kernels run on.  Index: DPSO_PHASE_*. */
+#define DPSO_PHASE_MOVE 0     /* Eqs. (velocity), (position), fitness, pbest */
+#define DPSO_PHASE_MUTATION 1 /* Sec. 3.2.2 */
+#define DPSO_PHASE_GBEST 2    /* both gbest passes */
+#define DPSO_PHASE_TWO_OPT 3  /* Sec. 3.2.3 */
+#define DPSO_NUM_PHASES 4
+typedef struct dpso_timing {
+    double ms[DPSO_NUM_PHASES];       /* summed device milliseconds */
+    int64_t launches[DPSO_NUM_PHASES]; /* kernels launched */
+    int32_t generations;               /* generations timed */
+    int32_t reserved;
+} dpso_timing;
+
 typedef struct dpso_swarm dpso_swarm;
 
 /* Fills the defaults: w=1, phi1=phi2=0.4 (Sec. 4), swarm=100, mut_period=3,
@@ -125,7 +140,8 @@ int dpso_cost_matrix(const double *xyz_dev, int32_t n, const double *boxes_dev, 
 /*
  * Tour cost, Eq. (min): cost_dev[t] = sum_k C[x_k][x_(k+1) mod n] for each of
  * `count` tours.  tours_dev: count x n uint16, row-major.  C_dev: n x n int32.
- * Asynchronous; inputs are not validated (tours must be permutations).
+ * Asynchronous.  Tours are not validated; a label outside [0, n) adds nothing
+ * and is never used to index C.
  */
 int dpso_fitness(const int32_t *C_dev, int32_t n, const uint16_t *tours_dev, int32_t count,
                  int64_t *cost_dev, void *stream);
@@ -173,6 +189,15 @@ int dpso_get_history(dpso_swarm *s, int64_t *gbest_host, int32_t cap, int32_t *l
 
 /* Counters; synchronises. */
 int dpso_get_stats(dpso_swarm *s, dpso_stats *st);
+
+/*
+ * Timing mode (tracing): while on, dpso_step launches each generation's
+ * kernels directly (not from a CUDA graph) with CUDA events between the
+ * phases; dpso_get_timing synchronises and returns the accumulated times.
+ * Turning it on clears the accumulators.  Results are identical either way.
+ */
+int dpso_set_timing(dpso_swarm *s, int on);
+int dpso_get_timing(dpso_swarm *s, dpso_timing *out);
 
 /*
  * Checkpoint: serialises the whole swarm (positions, velocities as

@@ -78,12 +78,18 @@ struct dpso_swarm {
     cudaStream_t last = nullptr;
     cudaStream_t cap = nullptr;
     cudaGraphExec_t g_plain = nullptr, g_mut = nullptr;
+    // timing mode
+    bool timing = false;
+    std::vector<cudaEvent_t> ev_pool;       // 5 events per timed generation
+    std::vector<std::array<int, 2>> pending; // (first event, mutation generation)
+    dpso_timing acc{};
 };
 
 namespace {
 
 void free_swarm(dpso_swarm* s) {
     if (!s) return;
+    for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->g_plain) cudaGraphExecDestroy(s->g_plain);
     if (s->g_mut) cudaGraphExecDestroy(s->g_mut);
     void* bufs[] = {s->C, s->X, s->V, s->P, s->G, s->F, s->PF, s->hash, s->dup, s->kept, s->ctl,
@@ -105,6 +111,8 @@ int dalloc(T** p, size_t count) {
     return DPSO_OK;
 }
 
+TwoOptArgs swarm_two_opt_args(dpso_swarm* s);
+
 // One generation of Fig. "pseudocode" enqueued on st: particle update, mutation
 // (when due), gbest, then the edge exchange and a second gbest pass (both
 // no-ops unless the first gbest pass scheduled the exchange).
@@ -113,26 +121,77 @@ cudaError_t enqueue_generation(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
     if (e == cudaSuccess && mut_iter) e = launch_mutation(s->k, s->d, st);
     if (e == cudaSuccess) e = launch_gbest(s->k, s->d, 0, mut_iter ? 1 : 0, st);
     if (e == cudaSuccess && (s->k.flags & DPSO_FLAG_TWO_OPT)) {
-        TwoOptArgs a{};
-        a.C = s->C;
-        a.ldc = s->k.ldc;
-        a.n = s->k.n;
-        a.tours = s->X;
-        a.ldt = s->k.ldn;
-        a.count = s->k.S;
-        a.cost = s->F;
-        a.pbest = s->P;
-        a.pcost = s->PF;
-        a.max_moves = s->k.max_moves;
-        a.gate = &s->ctl->run_two_opt;
-        a.queue = &s->ctl->queue;
-        a.pairs = &s->ctl->pairs;
-        a.moves = &s->ctl->moves;
-        a.status = &s->ctl->status;
-        e = launch_two_opt(a, s->num_sms, st);
+        e = launch_two_opt(swarm_two_opt_args(s), s->num_sms, st);
         if (e == cudaSuccess) e = launch_gbest(s->k, s->d, 1, mut_iter ? 1 : 0, st);
     }
     return e;
+}
+
+TwoOptArgs swarm_two_opt_args(dpso_swarm* s) {
+    TwoOptArgs a{};
+    a.C = s->C;
+    a.ldc = s->k.ldc;
+    a.n = s->k.n;
+    a.tours = s->X;
+    a.ldt = s->k.ldn;
+    a.count = s->k.S;
+    a.cost = s->F;
+    a.pbest = s->P;
+    a.pcost = s->PF;
+    a.max_moves = s->k.max_moves;
+    a.gate = &s->ctl->run_two_opt;
+    a.queue = &s->ctl->queue;
+    a.pairs = &s->ctl->pairs;
+    a.moves = &s->ctl->moves;
+    a.status = &s->ctl->status;
+    return a;
+}
+
+// Timing mode: the same kernels as enqueue_generation with events between the
+// phases (move | mutation | gbest | 2-opt | gbest).
+cudaError_t enqueue_generation_timed(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
+    const size_t base = s->pending.size() * 6;
+    while (s->ev_pool.size() < base + 6) {
+        cudaEvent_t e;
+        cudaError_t r = cudaEventCreate(&e);
+        if (r != cudaSuccess) return r;
+        s->ev_pool.push_back(e);
+    }
+    cudaEvent_t* ev = s->ev_pool.data() + base;
+    const bool two = (s->k.flags & DPSO_FLAG_TWO_OPT) != 0;
+    cudaError_t e = cudaEventRecord(ev[0], st);
+    if (e == cudaSuccess) e = launch_move(s->k, s->d, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
+    if (e == cudaSuccess && mut_iter) e = launch_mutation(s->k, s->d, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
+    if (e == cudaSuccess) e = launch_gbest(s->k, s->d, 0, mut_iter ? 1 : 0, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess && two) e = launch_two_opt(swarm_two_opt_args(s), s->num_sms, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
+    if (e == cudaSuccess && two) e = launch_gbest(s->k, s->d, 1, mut_iter ? 1 : 0, st);
+    if (e == cudaSuccess) e = cudaEventRecord(ev[5], st);
+    if (e == cudaSuccess) s->pending.push_back({static_cast<int>(base), mut_iter ? 1 : 0});
+    return e;
+}
+
+int collect_timing(dpso_swarm* s) {
+    for (const auto& pr : s->pending) {
+        cudaEvent_t* ev = s->ev_pool.data() + pr[0];
+        float t[5];
+        for (int q = 0; q < 5; ++q) CK(cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]));
+        const bool two = (s->k.flags & DPSO_FLAG_TWO_OPT) != 0;
+        s->acc.ms[DPSO_PHASE_MOVE] += t[0];
+        s->acc.ms[DPSO_PHASE_MUTATION] += t[1];
+        s->acc.ms[DPSO_PHASE_GBEST] += t[2] + t[4];
+        s->acc.ms[DPSO_PHASE_TWO_OPT] += t[3];
+        s->acc.launches[DPSO_PHASE_MOVE] += 1;
+        s->acc.launches[DPSO_PHASE_MUTATION] += pr[1] ? 4 : 0;
+        s->acc.launches[DPSO_PHASE_GBEST] += two ? 2 : 1;
+        s->acc.launches[DPSO_PHASE_TWO_OPT] += two ? 1 : 0;
+        s->acc.generations += 1;
+    }
+    s->pending.clear();
+    return DPSO_OK;
 }
 
 int capture(dpso_swarm* s, bool mut_iter, cudaGraphExec_t* out) {
@@ -439,7 +498,8 @@ int dpso_step(dpso_swarm* s, int32_t iterations, void* stream) {
     for (int it = 0; it < iterations; ++it) {
         const int t = s->t_host + 1 + it;
         const bool mut = (s->k.flags & DPSO_FLAG_MUTATION) && (t % s->k.mut_period == 0);
-        CK(cudaGraphLaunch(mut ? s->g_mut : s->g_plain, st));
+        if (s->timing) CK(enqueue_generation_timed(s, mut, st));
+        else CK(cudaGraphLaunch(mut ? s->g_mut : s->g_plain, st));
     }
     s->t_host += iterations;
     return DPSO_OK;
@@ -579,6 +639,26 @@ int dpso_set_state(dpso_swarm* s, const void* buf, size_t bytes) {
     c.runs = h.runs;
     CK(cudaMemcpy(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
     s->t_host = h.t;
+    return DPSO_OK;
+}
+
+int dpso_set_timing(dpso_swarm* s, int on) {
+    if (!s) return DPSO_ERR_ARG;
+    DeviceGuard g(s->device);
+    CK(cudaStreamSynchronize(s->last));
+    s->pending.clear();
+    s->acc = dpso_timing{};
+    s->timing = on != 0;
+    return DPSO_OK;
+}
+
+int dpso_get_timing(dpso_swarm* s, dpso_timing* out) {
+    if (!s || !out) return DPSO_ERR_ARG;
+    DeviceGuard g(s->device);
+    CK(cudaStreamSynchronize(s->last));
+    const int st = collect_timing(s);
+    if (st) return st;
+    *out = s->acc;
     return DPSO_OK;
 }
 

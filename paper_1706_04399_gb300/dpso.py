@@ -58,6 +58,14 @@ class dpso_stats(ctypes.Structure):
                 ("device_status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+PHASES = ("move", "mutation", "gbest", "two_opt")
+
+
+class dpso_timing(ctypes.Structure):
+    _fields_ = [("ms", ctypes.c_double * 4), ("launches", ctypes.c_int64 * 4),
+                ("generations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -91,6 +99,8 @@ def lib():
             "dpso_get_best": (ctypes.c_int, [_vp, _i32p, _i64p]),
             "dpso_get_history": (ctypes.c_int, [_vp, _i64p, _i32, _i32p]),
             "dpso_get_stats": (ctypes.c_int, [_vp, ctypes.POINTER(dpso_stats)]),
+            "dpso_set_timing": (ctypes.c_int, [_vp, ctypes.c_int]),
+            "dpso_get_timing": (ctypes.c_int, [_vp, ctypes.POINTER(dpso_timing)]),
             "dpso_get_state": (ctypes.c_int, [_vp, _vp, ctypes.POINTER(ctypes.c_size_t)]),
             "dpso_set_state": (ctypes.c_int, [_vp, _vp, ctypes.c_size_t]),
             "dpso_destroy": (None, [_vp]),
@@ -237,6 +247,16 @@ class Swarm:
         st = dpso_stats()
         _check(lib().dpso_get_stats(self._h, ctypes.byref(st)), "dpso_get_stats")
         return {k: getattr(st, k) for k, _ in dpso_stats._fields_ if k != "reserved"}
+
+    def set_timing(self, on: bool):
+        _check(lib().dpso_set_timing(self._h, 1 if on else 0), "dpso_set_timing")
+
+    def timing(self) -> dict:
+        t = dpso_timing()
+        _check(lib().dpso_get_timing(self._h, ctypes.byref(t)), "dpso_get_timing")
+        return {"ms": dict(zip(PHASES, list(t.ms))),
+                "launches": dict(zip(PHASES, list(t.launches))),
+                "generations": t.generations}
 
     def state_bytes(self) -> bytes:
         nb = ctypes.c_size_t(0)

@@ -196,3 +196,34 @@ def test_init_rejects_bad_arguments():
     with pytest.raises(dpso.DpsoError) as e:
         dpso.Swarm(C, 2, None, dpso.default_params(), 1)
     assert e.value.status == dpso.ERR_ARG
+
+
+@pytest.mark.parametrize("name,count,sample", [("facade", 256, [0, 101, 255]),
+                                               ("bridge", 64, [9, 63])])
+def test_full_size_two_opt_from_initial_tours(name, count, sample):
+    """The edge exchange at full size from random starting tours: the GPU runs
+    it on `count` initial particles, the oracle on a sample of them (both sides
+    build their own initial swarm; test_full_size_init_bitwise shows they agree)."""
+    inst = inputs.CONFIGS[name]()
+    C, C_np = _setup(inst)
+    S, n = inst.swarm, inst.n
+    gpu = dpso.Swarm(C, n, inst.tags, dpso.default_params(swarm=S), inst.seed)
+    X0 = gpu.state()["X"]
+    gpu.close()
+    first = S - count                     # random (not back-and-forth) particles
+    T = torch.from_numpy(X0[first:].view(np.int16).copy()).to(DEV)
+    cost = torch.empty(count, dtype=torch.int64, device=DEV)
+    pairs, moves = dpso.dpso_two_opt(C, n, T, count, cost)
+    got = T.cpu().numpy().view(np.uint16)
+    got_c = cost.cpu().numpy()
+    ref = oracle.Swarm(C_np, inst.tags, swarm=S, seed=inst.seed)
+    X0_ref = ref.state()["X"]
+    for k in sample:
+        y, f, mv, pr = oracle.two_opt(C_np, X0_ref[first + k])
+        assert np.array_equal(got[k], y), (name, k)
+        assert got_c[k] == f and mv > n // 4, (name, k, mv)
+    assert moves > count * (n // 4) and pairs % (n * (n - 3) // 2) == 0
+    for k in range(count):
+        assert np.array_equal(np.sort(got[k]), np.arange(n))
+    for k in range(0, count, max(1, count // 8)):
+        assert got_c[k] == oracle.fitness(C_np, got[k])

@@ -161,6 +161,28 @@ int dpso_two_opt(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t c
                  int64_t *moves_host, void *stream);
 
 /*
+ * dpso_two_opt without any device allocation (the paper has no counterpart;
+ * this is a deployment variant).  Same arguments, validation, results and
+ * synchronisation as dpso_two_opt.  Its scratch -- error word, work queue,
+ * totals and per-tour pass / move counts -- lives in one fixed 128 KiB device
+ * array inside the library (held by every GPU that loads it, until exit)
+ * instead of being allocated per call; it calls no allocating routine.
+ * For callers that must not allocate device memory while running: an on-board
+ * re-planning loop whose GPU memory is reserved once at start-up (an
+ * allocation can synchronise the device or fail under fragmentation in
+ * flight), or a process whose device memory belongs to another allocator.
+ * Limit: count <= DPSO_NOALLOC_MAX_TOURS, else DPSO_ERR_RANGE before any
+ * device work.  The first call on a device looks up the array's address with
+ * that device current: make it before any stream capture.  All calls share the
+ * array, so calls that overlap on the GPU (other streams, other host threads)
+ * race; the caller must serialise them.
+ */
+#define DPSO_NOALLOC_MAX_TOURS 16376
+int dpso_two_opt_noalloc(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t count,
+                         int64_t *cost_dev, int32_t max_moves, int64_t *pairs_host,
+                         int64_t *moves_host, void *stream);
+
+/*
  * Creates a swarm over the n x n cost matrix C_dev (copied; the caller may free
  * it after the call) and runs the initialisation block of Fig. "pseudocode":
  * positions (back-and-forth for a fraction, Sec. 3.2.1, else seeded random

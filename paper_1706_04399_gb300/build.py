@@ -29,6 +29,7 @@ SOURCES = {
     "swarm.cu": [],
     "two_opt.cu": [],
     "runtime.cu": [],
+    "two_opt_noalloc.cu": [],
 }
 
 

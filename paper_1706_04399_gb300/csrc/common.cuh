@@ -147,8 +147,15 @@ struct TwoOptArgs {
     unsigned long long* pairs;
     unsigned long long* moves;
     int* status;  // receives DPSO_ERR_INTERNAL if the move guard trips
+    // Optional per-tour counters: when tour_passes is set, each tour's passes
+    // and moves are written there instead of being added to *pairs / *moves.
+    unsigned int* tour_passes;
+    unsigned int* tour_moves;
 };
 cudaError_t launch_two_opt(const TwoOptArgs& a, int num_sms, cudaStream_t st);
+
+// ---- runtime.cu ----
+__global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err);
 int two_opt_rows(int n);
 
 }  // namespace dpso

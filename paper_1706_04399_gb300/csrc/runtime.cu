@@ -234,6 +234,10 @@ int read_ctl(dpso_swarm* s, Ctl* c) {
     return DPSO_OK;
 }
 
+}  // namespace
+
+namespace dpso {
+// Flags (bit 0 of *err) any of the count x n tours that is not a permutation.
 __global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err) {
     extern __shared__ unsigned char seen[];
     const uint16_t* x = tours + static_cast<size_t>(blockIdx.x) * n;
@@ -248,8 +252,7 @@ __global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err) {
     for (int i = threadIdx.x; i < n; i += blockDim.x)
         if (!seen[i]) atomicOr(err, 1);
 }
-
-}  // namespace
+}  // namespace dpso
 
 extern "C" {
 

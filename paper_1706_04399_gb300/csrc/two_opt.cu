@@ -181,8 +181,13 @@ __global__ void __launch_bounds__(kWarps * 32) two_opt_kernel(TwoOptArgs a) {
         for (int i = tid; i < n; i += blockDim.x) tour[i] = xs[i];
         if (tid == 0) {
             a.cost[p] = f;
-            atomicAdd(a.pairs, static_cast<unsigned long long>(passes) * npairs);
-            atomicAdd(a.moves, static_cast<unsigned long long>(moves));
+            if (a.tour_passes) {
+                a.tour_passes[p] = static_cast<unsigned int>(passes);
+                a.tour_moves[p] = static_cast<unsigned int>(moves);
+            } else {
+                atomicAdd(a.pairs, static_cast<unsigned long long>(passes) * npairs);
+                atomicAdd(a.moves, static_cast<unsigned long long>(moves));
+            }
             s_pf = a.pbest ? a.pcost[p] : LLONG_MIN;
         }
         __syncthreads();

@@ -93,6 +93,8 @@ def lib():
                                                 ctypes.POINTER(dpso_cost_params), _vp, _vp]),
             "dpso_fitness": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
             "dpso_two_opt": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p, _vp]),
+            "dpso_two_opt_noalloc": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p,
+                                                    _vp]),
             "dpso_init": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _i32, _vp,
                                          ctypes.POINTER(dpso_params), ctypes.c_uint64, _vp]),
             "dpso_step": (ctypes.c_int, [_vp, _i32, _vp]),
@@ -181,6 +183,20 @@ def dpso_two_opt(C_dev, n: int, tours_dev, count: int, cost_dev, max_moves: int 
     _check(lib().dpso_two_opt(_dev(C_dev), n, _dev(tours_dev), count, _dev(cost_dev), max_moves,
                               ctypes.byref(pairs), ctypes.byref(moves), _stream(stream)),
            "dpso_two_opt")
+    return pairs.value, moves.value
+
+
+NOALLOC_MAX_TOURS = 16376
+
+
+def dpso_two_opt_noalloc(C_dev, n: int, tours_dev, count: int, cost_dev, max_moves: int = 0,
+                         stream=None) -> tuple[int, int]:
+    """dpso_two_opt whose scratch is a fixed array in the library (no allocation)."""
+    pairs = ctypes.c_int64(0)
+    moves = ctypes.c_int64(0)
+    _check(lib().dpso_two_opt_noalloc(_dev(C_dev), n, _dev(tours_dev), count, _dev(cost_dev),
+                                      max_moves, ctypes.byref(pairs), ctypes.byref(moves),
+                                      _stream(stream)), "dpso_two_opt_noalloc")
     return pairs.value, moves.value
 
 

@@ -28,6 +28,7 @@ SOURCES = {
     "cost.cu": ["-fmad=false"],
     "swarm.cu": [],
     "two_opt.cu": [],
+    "two_opt_tma.cu": [],
     "runtime.cu": [],
     "two_opt_noalloc.cu": [],
 }

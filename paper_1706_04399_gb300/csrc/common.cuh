@@ -135,6 +135,7 @@ size_t move_smem_bytes(const Consts& k, int warps);
 // be zero on entry.
 struct TwoOptArgs {
     const int* C;
+    const int* Cs;  // optional: four row-shifted copies of C (build_shifted_copies)
     int ldc, n;
     uint16_t* tours;
     int ldt, count;
@@ -153,6 +154,13 @@ struct TwoOptArgs {
     unsigned int* tour_moves;
 };
 cudaError_t launch_two_opt(const TwoOptArgs& a, int num_sms, cudaStream_t st);
+
+// ---- two_opt_tma.cu: TMA-staged variant (needs the shifted copies) ----
+__host__ __device__ int shifted_ld(int n);
+size_t two_opt_tma_smem(int n, int stages);
+int two_opt_tma_stages(int n, int* ctas_per_sm);  // 0 when n is too large
+cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStream_t st);
+cudaError_t launch_two_opt_tma(const TwoOptArgs& a, int num_sms, cudaStream_t st);
 
 // ---- runtime.cu ----
 __global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err);

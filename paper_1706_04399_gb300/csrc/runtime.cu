@@ -66,6 +66,7 @@ struct dpso_swarm {
     Consts k{};
     SwarmDev d{};
     int* C = nullptr;
+    int* Cs = nullptr;  // row-shifted copies of C for the TMA 2-opt (or null)
     uint16_t *X = nullptr, *V = nullptr, *P = nullptr, *G = nullptr;
     long long *F = nullptr, *PF = nullptr;
     unsigned long long* hash = nullptr;
@@ -92,7 +93,7 @@ void free_swarm(dpso_swarm* s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->g_plain) cudaGraphExecDestroy(s->g_plain);
     if (s->g_mut) cudaGraphExecDestroy(s->g_mut);
-    void* bufs[] = {s->C, s->X, s->V, s->P, s->G, s->F, s->PF, s->hash, s->dup, s->kept, s->ctl,
+    void* bufs[] = {s->C, s->Cs, s->X, s->V, s->P, s->G, s->F, s->PF, s->hash, s->dup, s->kept, s->ctl,
                     s->hist};
     for (void* b : bufs)
         if (b) cudaFree(b);
@@ -130,6 +131,7 @@ cudaError_t enqueue_generation(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
 TwoOptArgs swarm_two_opt_args(dpso_swarm* s) {
     TwoOptArgs a{};
     a.C = s->C;
+    a.Cs = s->Cs;
     a.ldc = s->k.ldc;
     a.n = s->k.n;
     a.tours = s->X;
@@ -330,11 +332,23 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
     }
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    int* Cs = nullptr;
+    int tma_ctas = 0;
+    if (e == cudaSuccess && herr == 0 && two_opt_tma_stages(n, &tma_ctas) > 0) {
+        if (cudaMallocAsync(&Cs, sizeof(int) * 4 * static_cast<size_t>(n) * shifted_ld(n), st) !=
+            cudaSuccess) {
+            cudaGetLastError();
+            Cs = nullptr;  // fall back to the kernel that stages rows itself
+        } else {
+            e = build_shifted_copies(C_dev, n, n, Cs, st);
+        }
+    }
     if (e == cudaSuccess && herr == 0) {
         e = launch_fitness(C_dev, n, n, tours_dev, n, count, reinterpret_cast<long long*>(cost_dev),
                            st);
         TwoOptArgs a{};
         a.C = C_dev;
+        a.Cs = Cs;
         a.ldc = n;
         a.n = n;
         a.tours = tours_dev;
@@ -352,9 +366,10 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
     }
     cudaFreeAsync(scratch, st);
+    if (Cs) cudaFreeAsync(Cs, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     if (e != cudaSuccess) return DPSO_ERR_CUDA;
-    if (herr == DPSO_ERR_INTERNAL) return DPSO_ERR_INTERNAL;
+    if (herr == DPSO_ERR_INTERNAL || herr == DPSO_ERR_TIMEOUT) return herr;
     if (herr & 1) return DPSO_ERR_ARG;
     if (herr & 2) return DPSO_ERR_RANGE;
     if (pairs_host) *pairs_host = static_cast<int64_t>(counters[0]);
@@ -465,6 +480,12 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
         return fail2(DPSO_ERR_CUDA);
     if (herr & 1) return fail2(DPSO_ERR_ARG);
     if (herr & 2) return fail2(DPSO_ERR_RANGE);
+    int tma_ctas = 0;
+    if ((p->flags & DPSO_FLAG_TWO_OPT) && two_opt_tma_stages(n, &tma_ctas) > 0) {
+        if ((st = dalloc(&s->Cs, static_cast<size_t>(4) * n * shifted_ld(n)))) return fail2(st);
+        if (build_shifted_copies(s->C, k.ldc, n, s->Cs, ust) != cudaSuccess)
+            return fail2(DPSO_ERR_CUDA);
+    }
 
     if (launch_init_particles(k, s->d, orders, s->n_det, ust) != cudaSuccess ||
         launch_fitness(s->C, k.ldc, n, s->X, k.ldn, k.S, s->F, ust) != cudaSuccess ||

@@ -125,7 +125,8 @@ def _two_opt_case(C_np, tours, max_moves=0):
 
 
 @pytest.mark.parametrize("n,count", [(3, 4), (4, 5), (5, 9), (6, 3), (33, 20), (34, 7),
-                                     (64, 16), (65, 16), (100, 40), (257, 6), (400, 4)])
+                                     (35, 6), (64, 16), (65, 16), (100, 40), (257, 6), (400, 4),
+                                     (600, 2), (820, 2)])
 def test_two_opt_to_convergence_bitwise(n, count):
     C_np = inputs.random_cost_matrix(n, 7 * n)
     _two_opt_case(C_np, inputs.random_tours(n, count, 3 * n))

@@ -28,7 +28,7 @@ SOURCES = {
     "cost.cu": ["-fmad=false"],
     "swarm.cu": [],
     "two_opt.cu": [],
-    "two_opt_tma.cu": [],
+    "two_opt_tiled.cu": [],
     "runtime.cu": [],
     "two_opt_noalloc.cu": [],
 }

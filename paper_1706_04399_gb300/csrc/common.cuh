@@ -155,12 +155,12 @@ struct TwoOptArgs {
 };
 cudaError_t launch_two_opt(const TwoOptArgs& a, int num_sms, cudaStream_t st);
 
-// ---- two_opt_tma.cu: TMA-staged variant (needs the shifted copies) ----
+// ---- two_opt_tiled.cu: pipelined tiled variant (needs the shifted copies) ----
 __host__ __device__ int shifted_ld(int n);
-size_t two_opt_tma_smem(int n, int stages);
-int two_opt_tma_stages(int n, int* ctas_per_sm);  // 0 when n is too large
+size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages);
+int two_opt_tiled_rows(int n);  // tile height, 0 when no height fits
 cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStream_t st);
-cudaError_t launch_two_opt_tma(const TwoOptArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_two_opt_tiled(const TwoOptArgs& a, int num_sms, cudaStream_t st);
 
 // ---- runtime.cu ----
 __global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err);

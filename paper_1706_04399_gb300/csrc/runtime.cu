@@ -333,8 +333,7 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
     if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
     int* Cs = nullptr;
-    int tma_ctas = 0;
-    if (e == cudaSuccess && herr == 0 && two_opt_tma_stages(n, &tma_ctas) > 0) {
+    if (e == cudaSuccess && herr == 0 && two_opt_tiled_rows(n) > 0) {
         if (cudaMallocAsync(&Cs, sizeof(int) * 4 * static_cast<size_t>(n) * shifted_ld(n), st) !=
             cudaSuccess) {
             cudaGetLastError();
@@ -480,8 +479,7 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
         return fail2(DPSO_ERR_CUDA);
     if (herr & 1) return fail2(DPSO_ERR_ARG);
     if (herr & 2) return fail2(DPSO_ERR_RANGE);
-    int tma_ctas = 0;
-    if ((p->flags & DPSO_FLAG_TWO_OPT) && two_opt_tma_stages(n, &tma_ctas) > 0) {
+    if ((p->flags & DPSO_FLAG_TWO_OPT) && two_opt_tiled_rows(n) > 0) {
         if ((st = dalloc(&s->Cs, static_cast<size_t>(4) * n * shifted_ld(n)))) return fail2(st);
         if (build_shifted_copies(s->C, k.ldc, n, s->Cs, ust) != cudaSuccess)
             return fail2(DPSO_ERR_CUDA);

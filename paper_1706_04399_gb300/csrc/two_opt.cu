@@ -227,8 +227,7 @@ int two_opt_rows(int n) {
 
 cudaError_t launch_two_opt(const TwoOptArgs& a, int num_sms, cudaStream_t st) {
     if (a.count <= 0) return cudaSuccess;
-    int per_sm = 0;
-    if (a.Cs && two_opt_tma_stages(a.n, &per_sm) > 0) return launch_two_opt_tma(a, num_sms, st);
+    if (a.Cs && two_opt_tiled_rows(a.n) > 0) return launch_two_opt_tiled(a, num_sms, st);
     switch (two_opt_rows(a.n)) {
         case 32: return launch_r<32>(a, num_sms, st);
         case 16: return launch_r<16>(a, num_sms, st);

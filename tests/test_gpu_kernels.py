@@ -139,10 +139,12 @@ def test_two_opt_grid_ties_bitwise():
     _two_opt_case(C_np, inputs.random_tours(144, 12, 5))
 
 
-@pytest.mark.parametrize("n,moves", [(1500, 12), (1700, 8), (3500, 4), (6600, 2), (8192, 1)])
+@pytest.mark.parametrize("n,moves", [(1500, 12), (1700, 8), (2300, 6), (3500, 4), (6600, 2),
+                                     (8192, 1)])
 def test_two_opt_large_tiles_capped_bitwise(n, moves):
-    # row-tile heights 32 / 16 / 8 / 4 at these sizes; capped move counts keep
-    # the oracle fast while still checking each pass exactly
+    # tiled kernel with 32 / 24 / 16 / 8-row tiles, then the general kernel
+    # (6600, 8192); capped move counts keep the oracle fast while still
+    # checking each pass exactly
     C_np = inputs.random_cost_matrix(n, n, hi=1_000_000)
     _two_opt_case(C_np, inputs.random_tours(n, 3, n), max_moves=moves)
 

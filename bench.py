@@ -15,7 +15,8 @@ value   particle-iterations/s = particles x generations / device time, with the
 e2e     the same metric through dpso_plan from pinned host buffers: copies in,
         cost matrix, initialisation, `steps` generations, best tour out.
 roofline  the 2-opt kernel: 8 bytes of C per candidate pair (two int32 entries)
-        over its CUDA-event time, against the L2 bandwidth measured in this run.
+        over its CUDA-event time, against the L2 read bandwidth measured in
+        this run (the cost matrix is L2-resident; rows are staged from L2).
 
 `--impl reference` times the CPU oracle on a bounded sample of the workload.
 """
@@ -192,25 +193,6 @@ def gpu_index_for_smi(local_rank: int) -> str | None:
     return str(local_rank)
 
 
-def l2_copy_gbs(torch) -> float:
-    """L2 bandwidth: best copy_ rate between two L2-resident 24 MiB buffers."""
-    n = 24 << 20
-    a = torch.ones(n, dtype=torch.uint8, device="cuda")
-    b = torch.empty_like(a)
-    for _ in range(5):
-        b.copy_(a)
-    best = float("inf")
-    s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    for _ in range(20):
-        s.record()
-        for _ in range(10):
-            b.copy_(a)
-        e.record()
-        e.synchronize()
-        best = min(best, s.elapsed_time(e) / 10)
-    return 2 * n / (best * 1e-3) / 1e9
-
-
 def measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
@@ -303,14 +285,15 @@ def gpu_line(args):
     out = None
     if rank == 0:
         peaks = measured_peaks()
-        l2 = l2_copy_gbs(torch)
+        l2 = dpso.dpso_probe_l2_read_gbs(24 << 20, 40)
         achieved = BYTES_PER_PAIR * pairs / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
         traffic = two_opt_traffic(inst.name)
         roofline = {
             "kernel": "two_opt_kernel", "bound": "l2", "achieved": achieved, "peak": l2,
             "unit": "GB/s", "frac": achieved / l2 if l2 else None,
             "traffic": traffic,
-            "peak_source": "L2 copy bandwidth measured in this run (24 MiB buffers)",
+            "peak_source": "L2 read bandwidth measured in this run by dpso_probe_l2_read_gbs "
+                           "(16-byte loads of a 24 MiB L2-resident buffer, best of 5)",
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
             "frac_of_hbm_peak": achieved / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
         }

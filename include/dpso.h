@@ -164,7 +164,8 @@ int dpso_two_opt(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t c
  * dpso_two_opt without any device allocation (the paper has no counterpart;
  * this is a deployment variant).  Same arguments, validation, results and
  * synchronisation as dpso_two_opt.  Its scratch -- error word, work queue,
- * totals and per-tour pass / move counts -- lives in one fixed 128 KiB device
+ * totals, the task descriptor and per-tour pass / move counts -- lives in one
+ * fixed 128 KiB device
  * array inside the library (held by every GPU that loads it, until exit)
  * instead of being allocated per call; it calls no allocating routine.
  * For callers that must not allocate device memory while running: an on-board
@@ -177,7 +178,7 @@ int dpso_two_opt(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t c
  * array, so calls that overlap on the GPU (other streams, other host threads)
  * race; the caller must serialise them.
  */
-#define DPSO_NOALLOC_MAX_TOURS 16376
+#define DPSO_NOALLOC_MAX_TOURS 16350
 int dpso_two_opt_noalloc(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t count,
                          int64_t *cost_dev, int32_t max_moves, int64_t *pairs_host,
                          int64_t *moves_host, void *stream);
@@ -239,6 +240,31 @@ int dpso_set_state(dpso_swarm *s, const void *buf, size_t bytes);
 void dpso_destroy(dpso_swarm *s);
 
 /*
+ * Batches (many independent instances advanced together).  A batch groups
+ * existing swarms of any sizes (all on the current device, each in at most one
+ * batch in use at a time).  dpso_batch_step runs `iterations` generations of
+ * every member with one set of launches per generation, replayed from a CUDA
+ * graph: one warp per particle of every member for Eqs. (velocity) and
+ * (position), one block per member for the gbest, and one persistent 2-opt
+ * launch over every member's tours (Sec. 3.2.3), longest tours first.  Each
+ * member follows exactly the trajectory it would follow alone (its arithmetic
+ * reads only its own data and its own counter-based random stream).  The
+ * members remain usable through the dpso_get_* calls; do not step a member
+ * alone while its batch is in use.  The batch owns only descriptors; destroy
+ * it before its members.  dpso_batch_create synchronises `stream`.
+ */
+typedef struct dpso_batch dpso_batch;
+int dpso_batch_create(dpso_batch **out, dpso_swarm *const *swarms, int32_t count, void *stream);
+int dpso_batch_step(dpso_batch *b, int32_t iterations, void *stream);
+/* Picks the 2-opt tile height (32 / 24 / 16 / 8 rows) for this batch by timing
+ * each candidate on scratch copies of the members' current tours (best called
+ * right after creation, when the tours are unsorted).  Results do not depend
+ * on the choice.  *rows_out (may be NULL) receives the height in use.
+ * Synchronises `stream`. */
+int dpso_batch_autotune(dpso_batch *b, int32_t *rows_out, void *stream);
+void dpso_batch_destroy(dpso_batch *b);
+
+/*
  * Synchronous convenience solve from host buffers: copies the inputs to the
  * device, builds the cost matrix, initialises a swarm, runs `iterations`
  * generations and copies the best tour (n int32) and cost back.  boxes_host
@@ -256,6 +282,15 @@ int dpso_plan(const double *xyz_host, int32_t n, const double *boxes_host, int32
  */
 int dpso_philox_draws(uint64_t seed, uint32_t phase, uint32_t iteration, uint32_t particle,
                       int32_t count, uint32_t *out_dev, void *stream);
+
+/*
+ * Measurement aid (no counterpart in the paper): the device's L2 read
+ * bandwidth in GB/s, the bound on staging cost-matrix rows in the 2-opt
+ * kernel.  Reads an L2-resident device buffer of `bytes` (allocated and freed
+ * by the call) `reps` times with 16-byte loads from every SM; best of five
+ * timed runs with CUDA events on `stream`.  Synchronises `stream`.
+ */
+int dpso_probe_l2_read_gbs(size_t bytes, int32_t reps, double *gbs, void *stream);
 
 #ifdef __cplusplus
 }

@@ -31,6 +31,7 @@ SOURCES = {
     "two_opt_tiled.cu": [],
     "runtime.cu": [],
     "two_opt_noalloc.cu": [],
+    "probe.cu": [],
 }
 
 

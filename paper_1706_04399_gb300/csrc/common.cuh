@@ -112,6 +112,41 @@ cudaError_t launch_check_inputs(const double* xyz, int n, const double* boxes, i
                                 cudaStream_t st);
 cudaError_t launch_check_cost(const int* C, int n, int ldc, int* err, cudaStream_t st);
 
+// One swarm as the generation kernels see it.
+struct SwarmDesc {
+    Consts k;
+    SwarmDev d;
+};
+
+// Swarms advanced together by one set of launches: desc[ninst] and
+// off[ninst + 1] (prefix sums of the swarm sizes) live in device memory.  A
+// single swarm is a batch of one.  Every instance's arithmetic depends only on
+// its own data, so results do not depend on the company it keeps.
+struct BatchView {
+    const SwarmDesc* desc;
+    const int* off;
+    int ninst;
+    int total;    // off[ninst]: particles in the batch
+    int max_ldn;  // largest ldn: sizes the move kernel's shared memory
+    int arrays;   // shared arrays per particle in the move kernel: 7 if any w < 1, else 5
+};
+
+// Instance owning global item g: the largest i with off[i] <= g.
+__device__ __forceinline__ int find_inst(const int* __restrict__ off, int ninst, int g) {
+    int lo = 0, hi = ninst - 1;
+    while (lo < hi) {
+        const int mid = (lo + hi + 1) >> 1;
+        if (off[mid] <= g) lo = mid;
+        else hi = mid - 1;
+    }
+    return lo;
+}
+
+// True when instance `k`'s running generation (t + 1) is a mutation generation.
+__device__ __forceinline__ bool mutation_due(const Consts& k, const Ctl* c) {
+    return !c->done && (k.flags & DPSO_FLAG_MUTATION) && ((c->t + 1) % k.mut_period == 0);
+}
+
 // ---- launchers (swarm.cu) ----
 cudaError_t launch_fitness(const int* C, int ldc, int n, const uint16_t* tours, int ldt, int count,
                            long long* out, cudaStream_t st);
@@ -120,20 +155,17 @@ cudaError_t launch_det_orders(const int* tags, int n, uint16_t* orders, int ldn,
 cudaError_t launch_init_particles(const Consts& k, const SwarmDev& d, const uint16_t* orders,
                                   int n_det, cudaStream_t st);
 cudaError_t launch_gbest_init(const Consts& k, const SwarmDev& d, cudaStream_t st);
-cudaError_t launch_move(const Consts& k, const SwarmDev& d, cudaStream_t st);
-cudaError_t launch_mutation(const Consts& k, const SwarmDev& d, cudaStream_t st);
-cudaError_t launch_gbest(const Consts& k, const SwarmDev& d, int second, int mut_iter,
-                         cudaStream_t st);
+cudaError_t launch_move(const BatchView& b, cudaStream_t st);
+cudaError_t launch_mutation(const BatchView& b, cudaStream_t st);
+cudaError_t launch_gbest(const BatchView& b, int second, cudaStream_t st);
 cudaError_t launch_philox_draws(unsigned long long seed, uint32_t phase, uint32_t iter,
                                 uint32_t particle, int count, uint32_t* out, cudaStream_t st);
-size_t move_smem_bytes(const Consts& k, int warps);
 
-// ---- launchers (two_opt.cu) ----
-// Runs best-improvement 2-opt on `count` tours of length n (row stride ldt),
-// updating tours, costs and (when pbest != nullptr) the pbest arrays.  When
-// `gate` is non-null the kernel does nothing unless *gate != 0.  queue must
-// be zero on entry.
-struct TwoOptArgs {
+// ---- launchers (two_opt.cu, two_opt_tiled.cu) ----
+// One 2-opt problem: best-improvement 2-opt on `count` tours of length n (row
+// stride ldt), updating tours, costs and (when pbest != nullptr) the pbest
+// arrays.  When `gate` is non-null nothing happens unless *gate != 0.
+struct TwoOptTask {
     const int* C;
     const int* Cs;  // optional: four row-shifted copies of C (build_shifted_copies)
     int ldc, n;
@@ -143,8 +175,8 @@ struct TwoOptArgs {
     uint16_t* pbest;
     long long* pcost;
     int max_moves;
+    int pad;
     const int* gate;
-    unsigned int* queue;
     unsigned long long* pairs;
     unsigned long long* moves;
     int* status;  // receives DPSO_ERR_INTERNAL if the move guard trips
@@ -153,14 +185,28 @@ struct TwoOptArgs {
     unsigned int* tour_passes;
     unsigned int* tour_moves;
 };
-cudaError_t launch_two_opt(const TwoOptArgs& a, int num_sms, cudaStream_t st);
+
+// One persistent launch over every tour of several problems: tasks[nprob] and
+// off[nprob + 1] (prefix sums of the counts) in device memory, one work queue
+// (zero on entry).
+struct TwoOptBatch {
+    const TwoOptTask* tasks;
+    const int* off;
+    int nprob, total;
+    int max_n;        // sizes shared memory and the tile height
+    bool shifted;     // every task has Cs: the tiled kernel may be used
+    int rows;         // tile height of the tiled kernel (0: the default for max_n)
+    unsigned int* queue;
+};
+cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 
 // ---- two_opt_tiled.cu: pipelined tiled variant (needs the shifted copies) ----
 __host__ __device__ int shifted_ld(int n);
 size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages);
-int two_opt_tiled_rows(int n);  // tile height, 0 when no height fits
+int two_opt_tiled_rows(int n);  // default tile height, 0 when no height fits
 cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStream_t st);
-cudaError_t launch_two_opt_tiled(const TwoOptArgs& a, int num_sms, cudaStream_t st);
+cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int num_sms, cudaStream_t st);
+cudaError_t launch_two_opt_general(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 
 // ---- runtime.cu ----
 __global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err);

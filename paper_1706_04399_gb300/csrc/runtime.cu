@@ -58,6 +58,16 @@ struct StateHeader {
     dpso_params prm;
 };
 
+// A swarm's descriptors as the batched launches read them (device memory).
+struct SwarmMeta {
+    SwarmDesc desc;
+    TwoOptTask task;
+    int off[2];   // particle offsets of a batch of one: {0, S}
+    int toff[2];  // tour offsets of the one 2-opt problem: {0, S}
+    unsigned int queue;
+    unsigned int pad;
+};
+
 }  // namespace
 
 struct dpso_swarm {
@@ -72,6 +82,7 @@ struct dpso_swarm {
     unsigned long long* hash = nullptr;
     unsigned char *dup = nullptr, *kept = nullptr;
     Ctl* ctl = nullptr;
+    SwarmMeta* meta = nullptr;  // device: descriptors of this swarm as a batch of one
     long long* hist = nullptr;
     int hist_cap = 0;
     int n_det = 0;
@@ -93,8 +104,8 @@ void free_swarm(dpso_swarm* s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->g_plain) cudaGraphExecDestroy(s->g_plain);
     if (s->g_mut) cudaGraphExecDestroy(s->g_mut);
-    void* bufs[] = {s->C, s->Cs, s->X, s->V, s->P, s->G, s->F, s->PF, s->hash, s->dup, s->kept, s->ctl,
-                    s->hist};
+    void* bufs[] = {s->C,   s->Cs,   s->X,   s->V,    s->P,   s->G,   s->F,
+                    s->PF,  s->hash, s->dup, s->kept, s->ctl, s->meta, s->hist};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->cap) cudaStreamDestroy(s->cap);
@@ -112,24 +123,9 @@ int dalloc(T** p, size_t count) {
     return DPSO_OK;
 }
 
-TwoOptArgs swarm_two_opt_args(dpso_swarm* s);
-
-// One generation of Fig. "pseudocode" enqueued on st: particle update, mutation
-// (when due), gbest, then the edge exchange and a second gbest pass (both
-// no-ops unless the first gbest pass scheduled the exchange).
-cudaError_t enqueue_generation(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
-    cudaError_t e = launch_move(s->k, s->d, st);
-    if (e == cudaSuccess && mut_iter) e = launch_mutation(s->k, s->d, st);
-    if (e == cudaSuccess) e = launch_gbest(s->k, s->d, 0, mut_iter ? 1 : 0, st);
-    if (e == cudaSuccess && (s->k.flags & DPSO_FLAG_TWO_OPT)) {
-        e = launch_two_opt(swarm_two_opt_args(s), s->num_sms, st);
-        if (e == cudaSuccess) e = launch_gbest(s->k, s->d, 1, mut_iter ? 1 : 0, st);
-    }
-    return e;
-}
-
-TwoOptArgs swarm_two_opt_args(dpso_swarm* s) {
-    TwoOptArgs a{};
+// Host-side copies of the descriptors the batched launches take.
+TwoOptTask swarm_task(const dpso_swarm* s) {
+    TwoOptTask a{};
     a.C = s->C;
     a.Cs = s->Cs;
     a.ldc = s->k.ldc;
@@ -142,11 +138,46 @@ TwoOptArgs swarm_two_opt_args(dpso_swarm* s) {
     a.pcost = s->PF;
     a.max_moves = s->k.max_moves;
     a.gate = &s->ctl->run_two_opt;
-    a.queue = &s->ctl->queue;
     a.pairs = &s->ctl->pairs;
     a.moves = &s->ctl->moves;
     a.status = &s->ctl->status;
     return a;
+}
+
+int swarm_arrays(const Consts& k) { return k.w_q >= (1ull << 32) ? 5 : 7; }
+
+BatchView swarm_view(const dpso_swarm* s) {
+    return BatchView{&s->meta->desc, s->meta->off, 1, s->k.S, s->k.ldn, swarm_arrays(s->k)};
+}
+
+TwoOptBatch swarm_two_opt(const dpso_swarm* s) {
+    return TwoOptBatch{&s->meta->task, s->meta->toff, 1, s->k.S, s->k.n, s->Cs != nullptr, 0,
+                       &s->meta->queue};
+}
+
+// Generation kernels for a batch view; `with_mutation` false skips the
+// mutation kernels (they would all be no-ops).  The edge exchange and its
+// gbest pass are gated per instance on the device.
+cudaError_t enqueue_batch_generation(const BatchView& bv, const TwoOptBatch& tb, bool any_two_opt,
+                                     bool with_mutation, int num_sms, cudaStream_t st) {
+    cudaError_t e = launch_move(bv, st);
+    if (e == cudaSuccess && with_mutation) e = launch_mutation(bv, st);
+    if (e == cudaSuccess) e = launch_gbest(bv, 0, st);
+    if (e == cudaSuccess && any_two_opt) {
+        e = cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st);
+        if (e == cudaSuccess) e = launch_two_opt(tb, num_sms, st);
+        if (e == cudaSuccess) e = launch_gbest(bv, 1, st);
+    }
+    return e;
+}
+
+// One generation of Fig. "pseudocode" for one swarm: particle update,
+// mutation (when due), gbest, then the edge exchange and a second gbest pass
+// (both no-ops unless the first gbest pass scheduled the exchange).
+cudaError_t enqueue_generation(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
+    return enqueue_batch_generation(swarm_view(s), swarm_two_opt(s),
+                                    (s->k.flags & DPSO_FLAG_TWO_OPT) != 0, mut_iter, s->num_sms,
+                                    st);
 }
 
 // Timing mode: the same kernels as enqueue_generation with events between the
@@ -161,16 +192,19 @@ cudaError_t enqueue_generation_timed(dpso_swarm* s, bool mut_iter, cudaStream_t 
     }
     cudaEvent_t* ev = s->ev_pool.data() + base;
     const bool two = (s->k.flags & DPSO_FLAG_TWO_OPT) != 0;
+    const BatchView bv = swarm_view(s);
+    const TwoOptBatch tb = swarm_two_opt(s);
     cudaError_t e = cudaEventRecord(ev[0], st);
-    if (e == cudaSuccess) e = launch_move(s->k, s->d, st);
+    if (e == cudaSuccess) e = launch_move(bv, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess && mut_iter) e = launch_mutation(s->k, s->d, st);
+    if (e == cudaSuccess && mut_iter) e = launch_mutation(bv, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-    if (e == cudaSuccess) e = launch_gbest(s->k, s->d, 0, mut_iter ? 1 : 0, st);
+    if (e == cudaSuccess) e = launch_gbest(bv, 0, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
-    if (e == cudaSuccess && two) e = launch_two_opt(swarm_two_opt_args(s), s->num_sms, st);
+    if (e == cudaSuccess && two) e = cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess && two) e = launch_two_opt(tb, s->num_sms, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
-    if (e == cudaSuccess && two) e = launch_gbest(s->k, s->d, 1, mut_iter ? 1 : 0, st);
+    if (e == cudaSuccess && two) e = launch_gbest(bv, 1, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[5], st);
     if (e == cudaSuccess) s->pending.push_back({static_cast<int>(base), mut_iter ? 1 : 0});
     return e;
@@ -315,16 +349,25 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
     int dev = 0, sms = 0;
     CK(cudaGetDevice(&dev));
     CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    // scratch: [0] error word, [1] queue, [2..3] pairs, [4..5] moves
-    unsigned int* scratch = nullptr;
-    if (cudaMallocAsync(&scratch, 8 * sizeof(unsigned int), st) != cudaSuccess) {
+    // scratch: error word, work queue, counters, and the one-problem task list
+    struct Scratch {
+        int err;
+        unsigned int queue;
+        unsigned long long pairs, moves;
+        TwoOptTask task;
+        int toff[2];
+    };
+    Scratch* scratch = nullptr;
+    if (cudaMallocAsync(&scratch, sizeof(Scratch), st) != cudaSuccess) {
         cudaGetLastError();
         return DPSO_ERR_NO_MEMORY;
     }
-    int* err = reinterpret_cast<int*>(scratch);
+    int* err = &scratch->err;
     int herr = 0;
     unsigned long long counters[2] = {0, 0};
-    cudaError_t e = cudaMemsetAsync(scratch, 0, 8 * sizeof(unsigned int), st);
+    Scratch host{};
+    host.toff[1] = count;
+    cudaError_t e = cudaMemcpyAsync(scratch, &host, sizeof(Scratch), cudaMemcpyHostToDevice, st);
     if (e == cudaSuccess) e = launch_check_cost(C_dev, n, n, err, st);
     if (e == cudaSuccess) {
         tours_valid_kernel<<<count, 256, n, st>>>(tours_dev, n, err);
@@ -345,7 +388,7 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
     if (e == cudaSuccess && herr == 0) {
         e = launch_fitness(C_dev, n, n, tours_dev, n, count, reinterpret_cast<long long*>(cost_dev),
                            st);
-        TwoOptArgs a{};
+        TwoOptTask& a = host.task;
         a.C = C_dev;
         a.Cs = Cs;
         a.ldc = n;
@@ -355,14 +398,20 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
         a.count = count;
         a.cost = reinterpret_cast<long long*>(cost_dev);
         a.max_moves = max_moves;
-        a.queue = scratch + 1;
-        a.pairs = reinterpret_cast<unsigned long long*>(scratch + 2);
-        a.moves = reinterpret_cast<unsigned long long*>(scratch + 4);
+        a.pairs = &scratch->pairs;
+        a.moves = &scratch->moves;
         a.status = err;
-        if (e == cudaSuccess) e = launch_two_opt(a, sms, st);
         if (e == cudaSuccess)
-            e = cudaMemcpyAsync(counters, scratch + 2, sizeof(counters), cudaMemcpyDeviceToHost, st);
+            e = cudaMemcpyAsync(&scratch->task, &host.task, sizeof(TwoOptTask),
+                                cudaMemcpyHostToDevice, st);
+        const TwoOptBatch tb{&scratch->task, scratch->toff, 1, count, n, Cs != nullptr, 0,
+                             &scratch->queue};
+        if (e == cudaSuccess) e = launch_two_opt(tb, sms, st);
+        if (e == cudaSuccess)
+            e = cudaMemcpyAsync(counters, &scratch->pairs, sizeof(counters), cudaMemcpyDeviceToHost,
+                                st);
         if (e == cudaSuccess) e = cudaMemcpyAsync(&herr, err, sizeof(int), cudaMemcpyDeviceToHost, st);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(st);  // host.task is read by the copy
     }
     cudaFreeAsync(scratch, st);
     if (Cs) cudaFreeAsync(Cs, st);
@@ -441,7 +490,7 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
         (st = dalloc(&s->V, S * ldn)) || (st = dalloc(&s->P, S * ldn)) ||
         (st = dalloc(&s->G, ldn)) || (st = dalloc(&s->F, S)) || (st = dalloc(&s->PF, S)) ||
         (st = dalloc(&s->hash, S)) || (st = dalloc(&s->dup, S)) || (st = dalloc(&s->kept, S)) ||
-        (st = dalloc(&s->ctl, 1)))
+        (st = dalloc(&s->ctl, 1)) || (st = dalloc(&s->meta, 1)))
         return fail(st);
     if ((st = ensure_history(s, 1024))) return fail(st);
     // the zero-fills above ran on the legacy stream; the caller's stream may
@@ -482,6 +531,17 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
     if ((p->flags & DPSO_FLAG_TWO_OPT) && two_opt_tiled_rows(n) > 0) {
         if ((st = dalloc(&s->Cs, static_cast<size_t>(4) * n * shifted_ld(n)))) return fail2(st);
         if (build_shifted_copies(s->C, k.ldc, n, s->Cs, ust) != cudaSuccess)
+            return fail2(DPSO_ERR_CUDA);
+    }
+    {
+        SwarmMeta m{};
+        m.desc.k = k;
+        m.desc.d = s->d;
+        m.task = swarm_task(s);
+        m.off[1] = k.S;
+        m.toff[1] = k.S;
+        if (cudaMemcpyAsync(s->meta, &m, sizeof(m), cudaMemcpyHostToDevice, ust) != cudaSuccess ||
+            cudaStreamSynchronize(ust) != cudaSuccess)
             return fail2(DPSO_ERR_CUDA);
     }
 
@@ -689,6 +749,252 @@ void dpso_destroy(dpso_swarm* s) {
     DeviceGuard g(s->device);
     cudaStreamSynchronize(s->last);
     free_swarm(s);
+}
+
+// ------------------------------------------------------------------ batches
+
+}  // extern "C"
+
+struct dpso_batch {
+    int device = 0, num_sms = 0;
+    std::vector<dpso_swarm*> members;
+    SwarmDesc* desc = nullptr;  // device, members in creation order
+    int* off = nullptr;         // device, ninst + 1
+    TwoOptTask* tasks = nullptr;  // device, members by descending n
+    int* toff = nullptr;          // device, ninst + 1
+    unsigned int* queue = nullptr;
+    BatchView bv{};
+    TwoOptBatch tb{};
+    bool any_two_opt = false;
+    cudaStream_t cap = nullptr;
+    cudaGraphExec_t graph = nullptr;
+    cudaStream_t last = nullptr;
+};
+
+namespace {
+
+void free_batch(dpso_batch* b) {
+    if (!b) return;
+    if (b->graph) cudaGraphExecDestroy(b->graph);
+    void* bufs[] = {b->desc, b->off, b->tasks, b->toff, b->queue};
+    for (void* p : bufs)
+        if (p) cudaFree(p);
+    if (b->cap) cudaStreamDestroy(b->cap);
+    delete b;
+}
+
+int capture_batch(dpso_batch* b) {
+    if (b->graph) {
+        cudaGraphExecDestroy(b->graph);
+        b->graph = nullptr;
+    }
+    cudaGraph_t g = nullptr;
+    CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
+    const cudaError_t e =
+        enqueue_batch_generation(b->bv, b->tb, b->any_two_opt, true, b->num_sms, b->cap);
+    const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
+    if (e != cudaSuccess || e2 != cudaSuccess) {
+        if (g) cudaGraphDestroy(g);
+        return DPSO_ERR_CUDA;
+    }
+    const cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
+    cudaGraphDestroy(g);
+    return e3 == cudaSuccess ? DPSO_OK : DPSO_ERR_CUDA;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dpso_batch_create(dpso_batch** out, dpso_swarm* const* swarms, int32_t count, void* stream) {
+    if (!out || !swarms || count < 1) return DPSO_ERR_ARG;
+    *out = nullptr;
+    int dev = 0;
+    CK(cudaGetDevice(&dev));
+    for (int i = 0; i < count; ++i) {
+        if (!swarms[i] || swarms[i]->device != dev) return DPSO_ERR_ARG;
+        for (int j = 0; j < i; ++j)
+            if (swarms[j] == swarms[i]) return DPSO_ERR_ARG;
+    }
+    dpso_batch* b = new dpso_batch();
+    b->device = dev;
+    b->last = static_cast<cudaStream_t>(stream);
+    b->members.assign(swarms, swarms + count);
+    auto fail = [&](int code) {
+        free_batch(b);
+        return code;
+    };
+    if (cudaDeviceGetAttribute(&b->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+        return fail(DPSO_ERR_CUDA);
+    std::vector<SwarmDesc> desc(count);
+    std::vector<int> off(count + 1, 0);
+    int max_ldn = 0, max_n = 0, arrays = 5;
+    bool shifted = true;
+    for (int i = 0; i < count; ++i) {
+        const dpso_swarm* s = swarms[i];
+        desc[i].k = s->k;
+        desc[i].d = s->d;
+        off[i + 1] = off[i] + s->k.S;
+        max_ldn = std::max(max_ldn, s->k.ldn);
+        max_n = std::max(max_n, s->k.n);
+        arrays = std::max(arrays, swarm_arrays(s->k));
+        shifted = shifted && s->Cs != nullptr;
+        b->any_two_opt = b->any_two_opt || (s->k.flags & DPSO_FLAG_TWO_OPT);
+    }
+    // 2-opt work queue in order of decreasing tour length: long tours start first
+    std::vector<int> order(count);
+    for (int i = 0; i < count; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(),
+                     [&](int x, int y) { return swarms[x]->k.n > swarms[y]->k.n; });
+    std::vector<TwoOptTask> tasks;
+    std::vector<int> toff(1, 0);
+    for (int i : order) {
+        if (!(swarms[i]->k.flags & DPSO_FLAG_TWO_OPT)) continue;
+        tasks.push_back(swarm_task(swarms[i]));
+        toff.push_back(toff.back() + swarms[i]->k.S);
+    }
+    int st = DPSO_OK;
+    const int nt = static_cast<int>(tasks.size());
+    if ((st = dalloc(&b->desc, count)) || (st = dalloc(&b->off, count + 1)) ||
+        (st = dalloc(&b->tasks, std::max(nt, 1))) || (st = dalloc(&b->toff, nt + 1)) ||
+        (st = dalloc(&b->queue, 1)))
+        return fail(st);
+    if (cudaMemcpy(b->desc, desc.data(), sizeof(SwarmDesc) * count, cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaMemcpy(b->off, off.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        (nt > 0 && cudaMemcpy(b->tasks, tasks.data(), sizeof(TwoOptTask) * nt,
+                              cudaMemcpyHostToDevice) != cudaSuccess) ||
+        cudaMemcpy(b->toff, toff.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice) !=
+            cudaSuccess ||
+        cudaDeviceSynchronize() != cudaSuccess)
+        return fail(DPSO_ERR_CUDA);
+    b->bv = BatchView{b->desc, b->off, count, off[count], max_ldn, arrays};
+    b->tb = TwoOptBatch{b->tasks, b->toff, nt, toff.back(), max_n, shifted, 0, b->queue};
+    b->any_two_opt = nt > 0;
+    if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
+        return fail(DPSO_ERR_CUDA);
+    if ((st = capture_batch(b))) return fail(st);
+    *out = b;
+    return DPSO_OK;
+}
+
+int dpso_batch_step(dpso_batch* b, int32_t iterations, void* stream) {
+    if (!b || iterations < 0) return DPSO_ERR_ARG;
+    if (iterations == 0) return DPSO_OK;
+    DeviceGuard g(b->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    for (dpso_swarm* s : b->members) {
+        if (s->last != st) {
+            CK(cudaStreamSynchronize(s->last));
+            s->last = st;
+        }
+        const int r = ensure_history(s, s->t_host + iterations);
+        if (r) return r;
+    }
+    if (b->last != st) {
+        CK(cudaStreamSynchronize(b->last));
+        b->last = st;
+    }
+    for (int it = 0; it < iterations; ++it) CK(cudaGraphLaunch(b->graph, st));
+    for (dpso_swarm* s : b->members) s->t_host += iterations;
+    return DPSO_OK;
+}
+
+int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, void* stream) {
+    if (!b) return DPSO_ERR_ARG;
+    DeviceGuard g(b->device);
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamSynchronize(b->last));
+    b->last = st;
+    int chosen = 0;
+    if (b->tb.nprob > 0 && b->tb.shifted && two_opt_tiled_rows(b->tb.max_n) > 0) {
+        // Time each tile height on scratch copies of every member's current
+        // tours, with the gates ignored; the choice cannot change results.
+        std::vector<TwoOptTask> tasks(b->tb.nprob);
+        CK(cudaMemcpy(tasks.data(), b->tasks, sizeof(TwoOptTask) * b->tb.nprob,
+                      cudaMemcpyDeviceToHost));
+        std::vector<void*> scratch;
+        int st2 = DPSO_OK;
+        for (TwoOptTask& t : tasks) {
+            uint16_t* tours = nullptr;
+            long long* cost = nullptr;
+            unsigned long long* cnt = nullptr;
+            int* status = nullptr;
+            if ((st2 = dalloc(&tours, static_cast<size_t>(t.count) * t.ldt)) ||
+                (st2 = dalloc(&cost, t.count)) || (st2 = dalloc(&cnt, 2)) ||
+                (st2 = dalloc(&status, 1)))
+                break;
+            scratch.insert(scratch.end(), {tours, cost, cnt, status});
+            t.tours = tours;
+            t.cost = cost;
+            t.pbest = nullptr;
+            t.pcost = nullptr;
+            t.gate = nullptr;
+            t.pairs = cnt;
+            t.moves = cnt + 1;
+            t.status = status;
+        }
+        TwoOptTask* dtasks = nullptr;
+        if (!st2 && !(st2 = dalloc(&dtasks, tasks.size()))) {
+            CK(cudaMemcpy(dtasks, tasks.data(), sizeof(TwoOptTask) * tasks.size(),
+                          cudaMemcpyHostToDevice));
+            cudaEvent_t e0, e1;
+            CK(cudaEventCreate(&e0));
+            CK(cudaEventCreate(&e1));
+            float best = 1e30f;
+            for (int rows : {32, 24, 16, 8}) {
+                if (two_opt_tiled_smem(b->tb.max_n, rows, 1) > 220 * 1024) continue;
+                // restore the tours, then time one exchange
+                std::vector<TwoOptTask> orig(b->tb.nprob);
+                CK(cudaMemcpy(orig.data(), b->tasks, sizeof(TwoOptTask) * b->tb.nprob,
+                              cudaMemcpyDeviceToHost));
+                for (size_t i = 0; i < tasks.size(); ++i) {
+                    CK(cudaMemcpy2DAsync(tasks[i].tours, sizeof(uint16_t) * tasks[i].ldt,
+                                         orig[i].tours, sizeof(uint16_t) * orig[i].ldt,
+                                         sizeof(uint16_t) * tasks[i].n, tasks[i].count,
+                                         cudaMemcpyDeviceToDevice, st));
+                    CK(cudaMemcpyAsync(tasks[i].cost, orig[i].cost,
+                                       sizeof(long long) * tasks[i].count,
+                                       cudaMemcpyDeviceToDevice, st));
+                }
+                TwoOptBatch tb = b->tb;
+                tb.tasks = dtasks;
+                tb.rows = rows;
+                CK(cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st));
+                CK(cudaEventRecord(e0, st));
+                CK(launch_two_opt_tiled(tb, rows, b->num_sms, st));
+                CK(cudaEventRecord(e1, st));
+                CK(cudaEventSynchronize(e1));
+                float ms = 0.f;
+                CK(cudaEventElapsedTime(&ms, e0, e1));
+                if (ms < best) {
+                    best = ms;
+                    chosen = rows;
+                }
+            }
+            cudaEventDestroy(e0);
+            cudaEventDestroy(e1);
+        }
+        CK(cudaStreamSynchronize(st));
+        if (dtasks) cudaFree(dtasks);
+        for (void* p : scratch) cudaFree(p);
+        if (st2) return st2;
+        if (chosen > 0 && chosen != b->tb.rows) {
+            b->tb.rows = chosen;
+            const int r = capture_batch(b);
+            if (r) return r;
+        }
+    }
+    if (rows_out) *rows_out = b->tb.rows > 0 ? b->tb.rows : two_opt_tiled_rows(b->tb.max_n);
+    return DPSO_OK;
+}
+
+void dpso_batch_destroy(dpso_batch* b) {
+    if (!b) return;
+    DeviceGuard g(b->device);
+    cudaStreamSynchronize(b->last);
+    free_batch(b);
 }
 
 int dpso_plan(const double* xyz_host, int32_t n, const double* boxes_host, int32_t m,

@@ -237,29 +237,39 @@ __device__ __forceinline__ int scaled_count(unsigned long long phi_q, uint32_t u
 //   1. full greedy passes give |P - x|, |G - x| (and |v|): lanes 0, 1 (2)
 //   2. truncated passes apply the first ka / kb (kw) transpositions
 //   3. v <- sigma_b o sigma_a o sigma_wv, x <- v o x, fitness, pbest
-template <bool kPartialInertia>
-__global__ void move_kernel(Consts k, SwarmDev d) {
+// One warp per particle of any instance in the batch.  Shared memory per
+// warp: ya/pa (copy of x moved toward P and its inverse), yb/pb (toward G),
+// ix (inverse of x) and, when the instance has w < 1, yw/pw (identity moved
+// toward the velocity permutation).
+//   1. full greedy passes give |P - x|, |G - x| (and |v|): lanes 0, 1 (2)
+//   2. truncated passes apply the first ka / kb (kw) transpositions
+//   3. v <- sigma_b o sigma_a o sigma_wv, x <- v o x, fitness, pbest
+__global__ void move_kernel(BatchView b) {
     extern __shared__ __align__(16) uint16_t sm[];
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    const int p = blockIdx.x * (blockDim.x >> 5) + warp;
-    if (p >= k.S) return;
+    const int g = blockIdx.x * (blockDim.x >> 5) + warp;
+    if (g >= b.total) return;
+    const int inst = find_inst(b.off, b.ninst, g);
+    const int p = g - b.off[inst];
+    const Consts k = b.desc[inst].k;
+    const SwarmDev d = b.desc[inst].d;
     const Ctl* ctl = d.ctl;
     if (ctl->done) return;
     const int t = ctl->t + 1;
     const int n = k.n, ldn = k.ldn;
-    constexpr int kArr = kPartialInertia ? 7 : 5;
-    uint16_t* ya = sm + (size_t)warp * kArr * ldn;
+    const bool partial = k.w_q < (1ull << 32);
+    uint16_t* ya = sm + static_cast<size_t>(warp) * b.arrays * b.max_ldn;
     uint16_t* pa = ya + ldn;
     uint16_t* yb = pa + ldn;
     uint16_t* pb = yb + ldn;
     uint16_t* ix = pb + ldn;
     uint16_t* yw = ix + ldn;
     uint16_t* pw = yw + ldn;
-    uint16_t* x = d.X + (size_t)p * ldn;
-    uint16_t* v = d.V + (size_t)p * ldn;
-    uint16_t* P = d.P + (size_t)p * ldn;
+    uint16_t* x = d.X + static_cast<size_t>(p) * ldn;
+    uint16_t* v = d.V + static_cast<size_t>(p) * ldn;
+    uint16_t* P = d.P + static_cast<size_t>(p) * ldn;
     const uint16_t* G = d.G;
-    const int lanes = kPartialInertia ? (k.w_q == 0 ? 2 : 3) : 2;
+    const int lanes = partial ? (k.w_q == 0 ? 2 : 3) : 2;
 
     auto reset = [&]() {
         for (int i = lane; i < n; i += 32) {
@@ -269,7 +279,7 @@ __global__ void move_kernel(Consts k, SwarmDev d) {
             pa[xi] = static_cast<uint16_t>(i);
             yb[i] = xi;
             pb[xi] = static_cast<uint16_t>(i);
-            if (kPartialInertia) {
+            if (partial) {
                 yw[i] = static_cast<uint16_t>(i);
                 pw[i] = static_cast<uint16_t>(i);
             }
@@ -280,7 +290,7 @@ __global__ void move_kernel(Consts k, SwarmDev d) {
         int c = 0;
         if (lane == 0) c = greedy_subtract(ya, pa, P, n, lim_a);
         else if (lane == 1) c = greedy_subtract(yb, pb, G, n, lim_b);
-        else if (kPartialInertia && lane == 2 && lanes == 3) c = greedy_subtract(yw, pw, v, n, lim_w);
+        else if (lane == 2 && lanes == 3) c = greedy_subtract(yw, pw, v, n, lim_w);
         __syncwarp();
         return c;
     };
@@ -292,15 +302,15 @@ __global__ void move_kernel(Consts k, SwarmDev d) {
     const Block4 r = philox(0, p, t, kPhaseVelocity, k.seed);
     const int ka = scaled_count(k.phi1_q, r.v[0], La);
     const int kb = scaled_count(k.phi2_q, r.v[1], Lb);
-    const int kw = kPartialInertia ? static_cast<int>((k.w_q * static_cast<unsigned long long>(
-                                                           lanes == 3 ? Lw : 0)) >> 32)
-                                   : 0;
+    const int kw = partial ? static_cast<int>(
+                                 (k.w_q * static_cast<unsigned long long>(lanes == 3 ? Lw : 0)) >> 32)
+                           : 0;
     reset();
     run(ka, kb, kw);
 
     // sigma_a(m) = ya[ix[m]], sigma_b(m) = yb[ix[m]]; new velocity into pa.
     for (int l = lane; l < n; l += 32) {
-        uint16_t m = kPartialInertia ? yw[l] : v[l];
+        uint16_t m = partial ? yw[l] : v[l];
         m = ya[ix[m]];
         m = yb[ix[m]];
         pa[l] = m;
@@ -339,10 +349,25 @@ __device__ __forceinline__ unsigned long long mix64(unsigned long long z) {
     return z ^ (z >> 31);
 }
 
-__global__ void mut_hash_kernel(Consts k, SwarmDev d) {
-    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (p >= k.S || d.ctl->done) return;
-    const uint16_t* x = d.X + (size_t)p * k.ldn;
+// Global particle g of the batch -> (instance, particle); false when g is past
+// the batch or the instance does not mutate in its running generation.
+__device__ __forceinline__ bool mut_item(const BatchView& b, int g, Consts& k, SwarmDev& d,
+                                         int& p) {
+    if (g >= b.total) return false;
+    const int inst = find_inst(b.off, b.ninst, g);
+    p = g - b.off[inst];
+    k = b.desc[inst].k;
+    d = b.desc[inst].d;
+    return mutation_due(k, d.ctl);
+}
+
+__global__ void mut_hash_kernel(BatchView b) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    Consts k;
+    SwarmDev d;
+    int p;
+    if (!mut_item(b, g, k, d, p)) return;
+    const uint16_t* x = d.X + static_cast<size_t>(p) * k.ldn;
     unsigned long long h = 0;
     for (int i = lane; i < k.n; i += 32)
         h += mix64((static_cast<unsigned long long>(i) << 16) | x[i]);
@@ -360,21 +385,26 @@ __device__ bool tours_equal(const uint16_t* a, const uint16_t* b, int ldn) {
     return true;
 }
 
-__global__ void mut_dup_kernel(Consts k, SwarmDev d) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= k.S || d.ctl->done) return;
+__global__ void mut_dup_kernel(BatchView b) {
+    Consts k;
+    SwarmDev d;
+    int p;
+    if (!mut_item(b, blockIdx.x * blockDim.x + threadIdx.x, k, d, p)) return;
     const long long fp = d.F[p];
     const unsigned long long hp = d.hash[p];
     unsigned char dup = 0;
     for (int q = 0; q < p && !dup; ++q)
         if (d.F[q] == fp && d.hash[q] == hp)
-            dup = tours_equal(d.X + (size_t)q * k.ldn, d.X + (size_t)p * k.ldn, k.ldn);
+            dup = tours_equal(d.X + static_cast<size_t>(q) * k.ldn,
+                              d.X + static_cast<size_t>(p) * k.ldn, k.ldn);
     d.dup[p] = dup;
 }
 
-__global__ void mut_kept_kernel(Consts k, SwarmDev d) {
-    const int p = blockIdx.x * blockDim.x + threadIdx.x;
-    if (p >= k.S || d.ctl->done) return;
+__global__ void mut_kept_kernel(BatchView b) {
+    Consts k;
+    SwarmDev d;
+    int p;
+    if (!mut_item(b, blockIdx.x * blockDim.x + threadIdx.x, k, d, p)) return;
     unsigned char kept = 0;
     if (!d.dup[p]) {
         const long long fp = d.F[p];
@@ -386,11 +416,14 @@ __global__ void mut_kept_kernel(Consts k, SwarmDev d) {
     d.kept[p] = kept;
 }
 
-__global__ void mut_apply_kernel(Consts k, SwarmDev d) {
-    const int p = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
-    if (p >= k.S || d.ctl->done || d.kept[p]) return;
+__global__ void mut_apply_kernel(BatchView b) {
+    const int g = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+    Consts k;
+    SwarmDev d;
+    int p;
+    if (!mut_item(b, g, k, d, p) || d.kept[p]) return;
     const int t = d.ctl->t + 1, n = k.n;
-    uint16_t* x = d.X + (size_t)p * k.ldn;
+    uint16_t* x = d.X + static_cast<size_t>(p) * k.ldn;
     if (lane == 0) {
         for (int q = 0; q < k.mut_swaps; ++q) {
             const uint32_t di = 2u * q, dj = 2u * q + 1u;
@@ -405,14 +438,14 @@ __global__ void mut_apply_kernel(Consts k, SwarmDev d) {
         }
     }
     __syncwarp();
-    uint16_t* v = d.V + (size_t)p * k.ldn;
+    uint16_t* v = d.V + static_cast<size_t>(p) * k.ldn;
     for (int i = lane; i < n; i += 32) v[i] = static_cast<uint16_t>(i);
     const long long f = tour_cost_warp(d.C, k.ldc, n, x, lane);
     const long long pf = d.PF[p];
     __syncwarp();
     if (lane == 0) d.F[p] = f;
     if (f < pf) {
-        uint16_t* P = d.P + (size_t)p * k.ldn;
+        uint16_t* P = d.P + static_cast<size_t>(p) * k.ldn;
         for (int i = lane; i < n; i += 32) P[i] = x[i];
         if (lane == 0) d.PF[p] = f;
     }
@@ -423,19 +456,24 @@ __global__ void mut_apply_kernel(Consts k, SwarmDev d) {
 // replaces the gbest only on strict improvement.  Pass 0 runs after the
 // particle loop (and mutation) and schedules the edge exchange; pass 1 runs
 // after the exchange.  The generation is closed (history, stall counter,
-// generation counter, stop flag) by the last pass that runs.
+// generation counter, stop flag) by the last pass that runs.  One block per
+// instance of the batch.
 
-__global__ void gbest_kernel(Consts k, SwarmDev d, int second, int mut_iter) {
+__global__ void gbest_kernel(BatchView b, int second) {
+    const Consts k = b.desc[blockIdx.x].k;
+    const SwarmDev d = b.desc[blockIdx.x].d;
     Ctl* c = d.ctl;
     if (c->done) return;
     if (second && !c->run_two_opt) return;
+    const bool mut_iter = mutation_due(k, c);
     const unsigned long long key = block_min_key(d.PF, k.S);
     const long long best = static_cast<long long>(key >> 16);
     const int bp = static_cast<int>(key & 0xffffu);
     const long long gf_old = c->gf;
     __syncthreads();
     if (best < gf_old)
-        for (int i = threadIdx.x; i < k.n; i += blockDim.x) d.G[i] = d.P[(size_t)bp * k.ldn + i];
+        for (int i = threadIdx.x; i < k.n; i += blockDim.x)
+            d.G[i] = d.P[static_cast<size_t>(bp) * k.ldn + i];
     if (threadIdx.x != 0) return;
     const int t = c->t + 1;
     if (!second) c->gf_start = gf_old;
@@ -446,7 +484,6 @@ __global__ void gbest_kernel(Consts k, SwarmDev d, int second, int mut_iter) {
     if (!second) {
         const bool run = (k.flags & DPSO_FLAG_TWO_OPT) && !improved && (k.trigger == 0 || mut_iter);
         c->run_two_opt = run ? 1 : 0;
-        c->queue = 0;
         if (run) {
             c->runs += 1;
             return;
@@ -465,18 +502,15 @@ __global__ void philox_draws_kernel(unsigned long long seed, uint32_t phase, uin
     if (d < count) out[d] = draw(seed, phase, iter, particle, static_cast<uint32_t>(d));
 }
 
-int move_warps(const Consts& k) {
-    const size_t per = (k.w_q >= (1ull << 32) ? 5 : 7) * (size_t)k.ldn * sizeof(uint16_t);
+// Warps per block of the move kernel: up to 8, within 200 KB of shared memory.
+int move_warps(const BatchView& b) {
+    const size_t per = static_cast<size_t>(b.arrays) * b.max_ldn * sizeof(uint16_t);
     int w = 8;
     while (w > 1 && per * w > 200 * 1024) --w;
     return w;
 }
 
 }  // namespace
-
-size_t move_smem_bytes(const Consts& k, int warps) {
-    return (k.w_q >= (1ull << 32) ? 5 : 7) * (size_t)k.ldn * sizeof(uint16_t) * warps;
-}
 
 cudaError_t launch_fitness(const int* C, int ldc, int n, const uint16_t* tours, int ldt, int count,
                            long long* out, cudaStream_t st) {
@@ -505,34 +539,31 @@ cudaError_t launch_gbest_init(const Consts& k, const SwarmDev& d, cudaStream_t s
     return cudaGetLastError();
 }
 
-cudaError_t launch_move(const Consts& k, const SwarmDev& d, cudaStream_t st) {
-    const int w = move_warps(k);
-    const size_t smem = move_smem_bytes(k, w);
-    const int blocks = (k.S + w - 1) / w;
-    if (k.w_q >= (1ull << 32)) {
-        cudaFuncSetAttribute(move_kernel<false>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem));
-        move_kernel<false><<<blocks, 32 * w, smem, st>>>(k, d);
-    } else {
-        cudaFuncSetAttribute(move_kernel<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                             static_cast<int>(smem));
-        move_kernel<true><<<blocks, 32 * w, smem, st>>>(k, d);
-    }
+cudaError_t launch_move(const BatchView& b, cudaStream_t st) {
+    if (b.total <= 0) return cudaSuccess;
+    const int w = move_warps(b);
+    const size_t smem = static_cast<size_t>(b.arrays) * b.max_ldn * sizeof(uint16_t) * w;
+    const cudaError_t e = cudaFuncSetAttribute(move_kernel,
+                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                               static_cast<int>(smem));
+    if (e != cudaSuccess) return e;
+    move_kernel<<<(b.total + w - 1) / w, 32 * w, smem, st>>>(b);
     return cudaGetLastError();
 }
 
-cudaError_t launch_mutation(const Consts& k, const SwarmDev& d, cudaStream_t st) {
-    const int wb = (k.S * 32 + 255) / 256, tb = (k.S + 255) / 256;
-    mut_hash_kernel<<<wb, 256, 0, st>>>(k, d);
-    mut_dup_kernel<<<tb, 256, 0, st>>>(k, d);
-    mut_kept_kernel<<<tb, 256, 0, st>>>(k, d);
-    mut_apply_kernel<<<wb, 256, 0, st>>>(k, d);
+cudaError_t launch_mutation(const BatchView& b, cudaStream_t st) {
+    if (b.total <= 0) return cudaSuccess;
+    const int wb = (b.total * 32 + 255) / 256, tb = (b.total + 255) / 256;
+    mut_hash_kernel<<<wb, 256, 0, st>>>(b);
+    mut_dup_kernel<<<tb, 256, 0, st>>>(b);
+    mut_kept_kernel<<<tb, 256, 0, st>>>(b);
+    mut_apply_kernel<<<wb, 256, 0, st>>>(b);
     return cudaGetLastError();
 }
 
-cudaError_t launch_gbest(const Consts& k, const SwarmDev& d, int second, int mut_iter,
-                         cudaStream_t st) {
-    gbest_kernel<<<1, 1024, 0, st>>>(k, d, second, mut_iter);
+cudaError_t launch_gbest(const BatchView& b, int second, cudaStream_t st) {
+    if (b.ninst <= 0) return cudaSuccess;
+    gbest_kernel<<<b.ninst, 1024, 0, st>>>(b, second);
     return cudaGetLastError();
 }
 

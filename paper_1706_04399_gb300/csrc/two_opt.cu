@@ -46,15 +46,8 @@ __host__ __device__ inline size_t two_opt_smem(int n, int R) {
 }
 
 template <int R>
-__global__ void __launch_bounds__(kWarps * 32) two_opt_kernel(TwoOptArgs a) {
-    if (a.gate && *a.gate == 0) return;
+__global__ void __launch_bounds__(kWarps * 32) two_opt_kernel(TwoOptBatch b) {
     extern __shared__ __align__(16) unsigned char smraw[];
-    const int n = a.n;
-    const int ldr = row_stride(n);
-    int* rows = reinterpret_cast<int*>(smraw);
-    int* dd = rows + static_cast<size_t>(R + 1) * ldr;
-    uint16_t* xs = reinterpret_cast<uint16_t*>(dd + (n + 3) / 4 * 4);
-
     __shared__ int s_rowmin[R];
     __shared__ int s_part, s_bd, s_bi, s_bj, s_ei, s_ej;
     __shared__ long long s_pf;
@@ -62,15 +55,27 @@ __global__ void __launch_bounds__(kWarps * 32) two_opt_kernel(TwoOptArgs a) {
     constexpr int kStreams = 32 / R;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int arow = lane % R, stream = lane / R;
-    const int* __restrict__ C = a.C;
-    const int ldc = a.ldc;
-    const long long npairs = static_cast<long long>(n) * (n - 3) / 2;
 
     for (;;) {
-        if (tid == 0) s_part = static_cast<int>(atomicAdd(a.queue, 1u));
+        if (tid == 0) s_part = static_cast<int>(atomicAdd(b.queue, 1u));
         __syncthreads();
-        const int p = s_part;
-        if (p >= a.count) break;
+        const int g = s_part;
+        if (g >= b.total) break;
+        const int prob = find_inst(b.off, b.nprob, g);
+        const int p = g - b.off[prob];
+        const TwoOptTask a = b.tasks[prob];
+        if (a.gate && *a.gate == 0) {  // this problem does not exchange edges now
+            __syncthreads();
+            continue;
+        }
+        const int n = a.n;
+        const int ldr = row_stride(n);
+        int* rows = reinterpret_cast<int*>(smraw);
+        int* dd = rows + static_cast<size_t>(R + 1) * ldr;
+        uint16_t* xs = reinterpret_cast<uint16_t*>(dd + (n + 3) / 4 * 4);
+        const int* __restrict__ C = a.C;
+        const int ldc = a.ldc;
+        const long long npairs = static_cast<long long>(n) * (n - 3) / 2;
         uint16_t* tour = a.tours + static_cast<size_t>(p) * a.ldt;
         for (int i = tid; i < n; i += blockDim.x) xs[i] = tour[i];
         __syncthreads();
@@ -201,8 +206,8 @@ __global__ void __launch_bounds__(kWarps * 32) two_opt_kernel(TwoOptArgs a) {
 }
 
 template <int R>
-cudaError_t launch_r(const TwoOptArgs& a, int num_sms, cudaStream_t st) {
-    const size_t smem = two_opt_smem(a.n, R);
+cudaError_t launch_r(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
+    const size_t smem = two_opt_smem(b.max_n, R);
     cudaError_t e = cudaFuncSetAttribute(two_opt_kernel<R>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
@@ -211,8 +216,8 @@ cudaError_t launch_r(const TwoOptArgs& a, int num_sms, cudaStream_t st) {
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two_opt_kernel<R>, kWarps * 32, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = max(1, min(a.count, per_sm * num_sms));
-    two_opt_kernel<R><<<grid, kWarps * 32, smem, st>>>(a);
+    const int grid = max(1, min(b.total, per_sm * num_sms));
+    two_opt_kernel<R><<<grid, kWarps * 32, smem, st>>>(b);
     return cudaGetLastError();
 }
 
@@ -225,16 +230,22 @@ int two_opt_rows(int n) {
     return 0;
 }
 
-cudaError_t launch_two_opt(const TwoOptArgs& a, int num_sms, cudaStream_t st) {
-    if (a.count <= 0) return cudaSuccess;
-    if (a.Cs && two_opt_tiled_rows(a.n) > 0) return launch_two_opt_tiled(a, num_sms, st);
-    switch (two_opt_rows(a.n)) {
-        case 32: return launch_r<32>(a, num_sms, st);
-        case 16: return launch_r<16>(a, num_sms, st);
-        case 8: return launch_r<8>(a, num_sms, st);
-        case 4: return launch_r<4>(a, num_sms, st);
+cudaError_t launch_two_opt_general(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
+    switch (two_opt_rows(b.max_n)) {
+        case 32: return launch_r<32>(b, num_sms, st);
+        case 16: return launch_r<16>(b, num_sms, st);
+        case 8: return launch_r<8>(b, num_sms, st);
+        case 4: return launch_r<4>(b, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
+}
+
+cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
+    if (b.total <= 0) return cudaSuccess;
+    if (b.shifted && two_opt_tiled_rows(b.max_n) > 0)
+        return launch_two_opt_tiled(b, b.rows > 0 ? b.rows : two_opt_tiled_rows(b.max_n), num_sms,
+                                    st);
+    return launch_two_opt_general(b, num_sms, st);
 }
 
 }  // namespace dpso

@@ -16,10 +16,14 @@ namespace dpso {
 namespace {
 
 // Scratch layout (32-bit words): [0] error word, [1] work queue, [2..3] pairs
-// total, [4..5] moves total, [6..15] unused, then `count` pass counts followed
-// by `count` move counts.
-constexpr int kHeaderWords = 16;
+// total, [4..5] moves total, [6..15] unused, [16..63] the task descriptor,
+// [64..65] its tour offsets, then `count` pass counts followed by `count` move
+// counts.
+constexpr int kTaskWord = 16;
+constexpr int kOffWord = 64;
+constexpr int kHeaderWords = 68;
 constexpr size_t kScratchBytes = 128 * 1024;
+static_assert(sizeof(TwoOptTask) <= (kOffWord - kTaskWord) * 4, "task descriptor does not fit");
 static_assert((kScratchBytes / 4 - kHeaderWords) / 2 == DPSO_NOALLOC_MAX_TOURS,
               "DPSO_NOALLOC_MAX_TOURS must match the scratch array");
 
@@ -111,7 +115,7 @@ extern "C" int dpso_two_opt_noalloc(const int32_t* C_dev, int32_t n, uint16_t* t
     if (header[0] & 2u) return DPSO_ERR_RANGE;
 
     e = launch_fitness(C_dev, n, n, tours_dev, n, count, reinterpret_cast<long long*>(cost_dev), st);
-    TwoOptArgs a{};
+    TwoOptTask a{};
     a.C = C_dev;
     a.ldc = n;
     a.n = n;
@@ -120,13 +124,20 @@ extern "C" int dpso_two_opt_noalloc(const int32_t* C_dev, int32_t n, uint16_t* t
     a.count = count;
     a.cost = reinterpret_cast<long long*>(cost_dev);
     a.max_moves = max_moves;
-    a.queue = scratch + 1;
     a.pairs = reinterpret_cast<unsigned long long*>(scratch + 2);
     a.moves = reinterpret_cast<unsigned long long*>(scratch + 4);
     a.status = err;
     a.tour_passes = scratch + kHeaderWords;
     a.tour_moves = scratch + kHeaderWords + count;
-    if (e == cudaSuccess) e = launch_two_opt(a, sms, st);
+    TwoOptTask* task = reinterpret_cast<TwoOptTask*>(scratch + kTaskWord);
+    int* toff = reinterpret_cast<int*>(scratch + kOffWord);
+    const int host_off[2] = {0, count};
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(task, &a, sizeof(TwoOptTask), cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess)
+        e = cudaMemcpyAsync(toff, host_off, sizeof(host_off), cudaMemcpyHostToDevice, st);
+    const TwoOptBatch tb{task, toff, 1, count, n, false, 0, scratch + 1};
+    if (e == cudaSuccess) e = launch_two_opt(tb, sms, st);
     if (e == cudaSuccess) {
         noalloc_totals_kernel<<<1, 256, 0, st>>>(scratch, count,
                                                  static_cast<long long>(n) * (n - 3) / 2);

@@ -101,13 +101,14 @@ namespace {
 constexpr int kPadCost = (1 << 30) + 1;
 
 template <int ROWS, int STAGES>
-__global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptArgs a) {
+__global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) {
     constexpr int kRows = ROWS;           // positions per tile, one per lane
     constexpr int kStaged = ROWS + 1;     // cost rows staged per tile
-    if (a.gate && *a.gate == 0) return;
     // One dynamic shared block seen through three element types (all arrays
-    // alias its start): STAGES tile buffers of 33 x ldq ints, then the column
-    // records (n + 4 int2, the last four padding), then the tour (n + 1 uint16).
+    // alias its start): STAGES tile buffers of kStaged x ldq ints, then the
+    // column records (n + 4 int2, the last four padding), then the tour
+    // (n + 1 uint16).  Offsets depend on the tour's n; the block is sized for
+    // the largest n of the launch.
     extern __shared__ __align__(128) int smi[];
     extern __shared__ __align__(128) int2 smi2[];
     extern __shared__ __align__(128) int4 smi4[];
@@ -117,43 +118,52 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptArgs a) {
     __shared__ int s_part, s_e0, s_e1;
     __shared__ long long s_pf;
 
-    const int n = a.n;
-    const int ldq = shifted_ld(n);
-    const int q16 = ldq / 4;
-    const int buf_words = kStaged * ldq;
-    const int rec2 = STAGES * buf_words / 2;  // int2 index of record 0 (even)
-    const int xs16 = (rec2 + n + 4) * 4;      // uint16 index of x_0
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int* __restrict__ C = a.C;
-    const int* __restrict__ Cs = a.Cs;
-    const int ldc = a.ldc;
-    const long long npairs = static_cast<long long>(n) * (n - 3) / 2;
-    const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
-    const int guard = 1000 + 100 * n;
-
-    // All threads: copy the cost rows of tile t into buffer t % STAGES.
-    auto stage = [&](int t) {
-        const int I = t * kRows;
-        const int count = min(kStaged, n - 1 - I);
-        const int boff = (t % STAGES) * buf_words;
-        for (int r = warp; r < count; r += kWarps) {
-            const int k = (r >> 3) & 3;
-            const char* src = reinterpret_cast<const char*>(
-                                  Cs + (static_cast<size_t>(k) * n + smu[xs16 + I + r]) * ldq) +
-                              lane * 16;
-            int* dst = smi + boff + r * ldq + lane * 4;
-#pragma unroll
-            for (int j = 0; j < 4; ++j)
-                if (j * 32 + lane < q16) cp_async16(dst + j * 128, src + j * 512);
-            for (int j = 4; j * 32 + lane < q16; ++j) cp_async16(dst + j * 128, src + j * 512);
-        }
-    };
 
     for (;;) {
-        if (tid == 0) s_part = static_cast<int>(atomicAdd(a.queue, 1u));
+        if (tid == 0) s_part = static_cast<int>(atomicAdd(b.queue, 1u));
         __syncthreads();
-        const int p = s_part;
-        if (p >= a.count) break;
+        const int g = s_part;
+        if (g >= b.total) break;
+        const int prob = find_inst(b.off, b.nprob, g);
+        const int p = g - b.off[prob];
+        const TwoOptTask a = b.tasks[prob];
+        if (a.gate && *a.gate == 0) {  // this problem does not exchange edges now
+            __syncthreads();
+            continue;
+        }
+        const int n = a.n;
+        const int ldq = shifted_ld(n);
+        const int q16 = ldq / 4;
+        const int buf_words = kStaged * ldq;
+        const int rec2 = STAGES * buf_words / 2;  // int2 index of record 0 (even)
+        const int xs16 = (rec2 + n + 4) * 4;      // uint16 index of x_0
+        const int* __restrict__ C = a.C;
+        const int* __restrict__ Cs = a.Cs;
+        const int ldc = a.ldc;
+        const long long npairs = static_cast<long long>(n) * (n - 3) / 2;
+        const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
+        const int guard = 1000 + 100 * n;
+
+        // All threads: copy the cost rows of tile t into buffer t % STAGES.
+        auto stage = [&](int t) {
+            const int I = t * kRows;
+            const int count = min(kStaged, n - 1 - I);
+            const int boff = (t % STAGES) * buf_words;
+            for (int r = warp; r < count; r += kWarps) {
+                const int k = (r >> 3) & 3;
+                const char* src =
+                    reinterpret_cast<const char*>(
+                        Cs + (static_cast<size_t>(k) * n + smu[xs16 + I + r]) * ldq) +
+                    lane * 16;
+                int* dst = smi + boff + r * ldq + lane * 4;
+#pragma unroll
+                for (int j = 0; j < 4; ++j)
+                    if (j * 32 + lane < q16) cp_async16(dst + j * 128, src + j * 512);
+                for (int j = 4; j * 32 + lane < q16; ++j) cp_async16(dst + j * 128, src + j * 512);
+            }
+        };
+
         uint16_t* tour = a.tours + static_cast<size_t>(p) * a.ldt;
         for (int i = tid; i < n; i += kThreads) smu[xs16 + i] = tour[i];
         if (tid == 0) smu[xs16 + n] = tour[0];
@@ -329,8 +339,8 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptArgs a) {
 }
 
 template <int ROWS, int STAGES>
-cudaError_t launch_cfg(const TwoOptArgs& a, int num_sms, cudaStream_t st) {
-    const size_t smem = two_opt_tiled_smem(a.n, ROWS, STAGES);
+cudaError_t launch_cfg(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
+    const size_t smem = two_opt_tiled_smem(b.max_n, ROWS, STAGES);
     cudaError_t e = cudaFuncSetAttribute(two_opt_tiled_kernel<ROWS, STAGES>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
@@ -340,8 +350,8 @@ cudaError_t launch_cfg(const TwoOptArgs& a, int num_sms, cudaStream_t st) {
                                                       kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = max(1, min(a.count, per_sm * num_sms));
-    two_opt_tiled_kernel<ROWS, STAGES><<<grid, kThreads, smem, st>>>(a);
+    const int grid = max(1, min(b.total, per_sm * num_sms));
+    two_opt_tiled_kernel<ROWS, STAGES><<<grid, kThreads, smem, st>>>(b);
     return cudaGetLastError();
 }
 
@@ -363,13 +373,14 @@ cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_two_opt_tiled(const TwoOptArgs& a, int num_sms, cudaStream_t st) {
-    if (!a.Cs) return cudaErrorInvalidValue;
-    switch (two_opt_tiled_rows(a.n)) {
-        case 32: return launch_cfg<32, 1>(a, num_sms, st);
-        case 24: return launch_cfg<24, 1>(a, num_sms, st);
-        case 16: return launch_cfg<16, 1>(a, num_sms, st);
-        case 8: return launch_cfg<8, 1>(a, num_sms, st);
+cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int num_sms, cudaStream_t st) {
+    if (!b.shifted || two_opt_tiled_smem(b.max_n, rows, 1) > 220 * 1024)
+        return cudaErrorInvalidValue;
+    switch (rows) {
+        case 32: return launch_cfg<32, 1>(b, num_sms, st);
+        case 24: return launch_cfg<24, 1>(b, num_sms, st);
+        case 16: return launch_cfg<16, 1>(b, num_sms, st);
+        case 8: return launch_cfg<8, 1>(b, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }

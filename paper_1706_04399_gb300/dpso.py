@@ -110,6 +110,13 @@ def lib():
                                          ctypes.POINTER(dpso_cost_params),
                                          ctypes.POINTER(dpso_params), ctypes.c_uint64, _i32,
                                          _i32p, _i64p]),
+            "dpso_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32,
+                                                 _vp]),
+            "dpso_batch_step": (ctypes.c_int, [_vp, _i32, _vp]),
+            "dpso_batch_autotune": (ctypes.c_int, [_vp, _i32p, _vp]),
+            "dpso_batch_destroy": (None, [_vp]),
+            "dpso_probe_l2_read_gbs": (ctypes.c_int, [ctypes.c_size_t, _i32,
+                                                      ctypes.POINTER(ctypes.c_double), _vp]),
             "dpso_philox_draws": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32,
                                                  ctypes.c_uint32, ctypes.c_uint32, _i32, _vp, _vp]),
         }
@@ -186,7 +193,15 @@ def dpso_two_opt(C_dev, n: int, tours_dev, count: int, cost_dev, max_moves: int 
     return pairs.value, moves.value
 
 
-NOALLOC_MAX_TOURS = 16376
+def dpso_probe_l2_read_gbs(nbytes: int = 24 << 20, reps: int = 40, stream=None) -> float:
+    """Measured L2 read bandwidth (GB/s) of the current device."""
+    out = ctypes.c_double(0.0)
+    _check(lib().dpso_probe_l2_read_gbs(nbytes, reps, ctypes.byref(out), _stream(stream)),
+           "dpso_probe_l2_read_gbs")
+    return out.value
+
+
+NOALLOC_MAX_TOURS = 16350
 
 
 def dpso_two_opt_noalloc(C_dev, n: int, tours_dev, count: int, cost_dev, max_moves: int = 0,
@@ -310,3 +325,31 @@ class Swarm:
 
 # StateHeader: 2 uint32 + 6 int32 + int64 + 3 uint64 + uint64 seed + dpso_params
 _HDR_SIZE = 8 + 24 + 8 + 24 + 8 + ctypes.sizeof(dpso_params)
+
+
+class Batch:
+    """Owns a dpso_batch over existing Swarm objects (kept alive by the batch)."""
+
+    def __init__(self, swarms, stream=None):
+        self.swarms = list(swarms)
+        arr = (_vp * len(self.swarms))(*[sw._h.value for sw in self.swarms])
+        h = _vp()
+        _check(lib().dpso_batch_create(ctypes.byref(h), arr, len(self.swarms), _stream(stream)),
+               "dpso_batch_create")
+        self._h = h
+
+    def step(self, iterations: int, stream=None):
+        _check(lib().dpso_batch_step(self._h, iterations, _stream(stream)), "dpso_batch_step")
+
+    def autotune(self, stream=None) -> int:
+        rows = ctypes.c_int32(0)
+        _check(lib().dpso_batch_autotune(self._h, ctypes.byref(rows), _stream(stream)),
+               "dpso_batch_autotune")
+        return rows.value
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().dpso_batch_destroy(self._h)
+            self._h = _vp()
+
+    __del__ = close

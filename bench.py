@@ -50,6 +50,10 @@ def _env_int(name, default):
 
 def workload(name: str):
     from paper_1706_04399_gb300 import inputs
+    if name == "batched":      # the oracle arm times one member of the batch
+        return inputs.batched()[0]
+    if name == "serving":      # ... or the first request of the stream
+        return inputs.serving(count=1)[0][1]
     return inputs.CONFIGS[name]()
 
 
@@ -204,7 +208,7 @@ def measured_peaks() -> dict:
 def two_opt_traffic(workload_name: str):
     """DRAM bytes per 2-opt launch from the committed ncu summary, if it was
     taken from the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_1706_04399_gb300", "csrc", "two_opt.cu")
+    src = os.path.join(ROOT, "paper_1706_04399_gb300", "csrc", "two_opt_tiled.cu")
     path = os.path.join(ROOT, "profiles", "two_opt_dram_traffic.json")
     try:
         digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
@@ -289,7 +293,7 @@ def gpu_line(args):
         achieved = BYTES_PER_PAIR * pairs / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
         traffic = two_opt_traffic(inst.name)
         roofline = {
-            "kernel": "two_opt_kernel", "bound": "l2", "achieved": achieved, "peak": l2,
+            "kernel": "two_opt_tiled_kernel", "bound": "l2", "achieved": achieved, "peak": l2,
             "unit": "GB/s", "frac": achieved / l2 if l2 else None,
             "traffic": traffic,
             "peak_source": "L2 read bandwidth measured in this run by dpso_probe_l2_read_gbs "
@@ -350,13 +354,183 @@ def gpu_line(args):
     return out
 
 
+# ------------------------------------------------ batched and served workloads
+
+def _same_state(a: dict, b: dict) -> bool:
+    import numpy as np
+    keys = ("X", "V", "P", "G", "F", "PF", "history")
+    return all(np.array_equal(a[k], b[k]) for k in keys) and (a["t"], a["gf"]) == (b["t"], b["gf"])
+
+
+def batched_line(args):
+    """Independent instances of uneven size advanced together by dpso_batch_*
+    (one set of launches per generation for all of them) against the same
+    instances stepped one launch sequence per instance; both from the same
+    initial swarms, so their trajectories must be identical."""
+    import torch
+
+    from paper_1706_04399_gb300 import dpso, inputs
+
+    torch.cuda.set_device(0)
+    insts = inputs.batched()[: args.instances]
+    stream = torch.cuda.current_stream()
+    Cs = []
+    for inst in insts:
+        C = torch.empty((inst.n, inst.n), dtype=torch.int32, device="cuda")
+        boxes = torch.from_numpy(inst.boxes.reshape(-1, 6)).cuda() if inst.m else None
+        dpso.dpso_cost_matrix(torch.from_numpy(inst.xyz).cuda(), inst.n, boxes, inst.m,
+                              dpso.default_cost_params(), C, stream)
+        Cs.append(C)
+
+    def swarms():
+        return [dpso.Swarm(C, i.n, i.tags, dpso.default_params(swarm=i.swarm), i.seed, stream)
+                for C, i in zip(Cs, insts)]
+
+    together, alone = swarms(), swarms()
+    batch = dpso.Batch(together, stream)
+    rows = batch.autotune(stream)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    S_total = sum(i.swarm for i in insts)
+
+    def run(step_fn, steps):
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+               for _ in range(steps)]
+        for k in range(steps):
+            flush.zero_()
+            evs[k][0].record(stream)
+            step_fn()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+        return sum(a.elapsed_time(b) for a, b in evs)
+
+    def solo_step():
+        for sw in alone:
+            sw.step(1, stream)
+
+    batch.step(args.warmup, stream)
+    for sw in alone:
+        sw.step(args.warmup, stream)
+    torch.cuda.synchronize()
+    st0 = [sw.stats() for sw in together]
+    sampler = ClockSampler(gpu_index_for_smi(0))
+    with sampler:
+        ms_batch = run(lambda: batch.step(1, stream), args.steps)
+        ms_solo = run(solo_step, args.steps)
+    st1 = [sw.stats() for sw in together]
+    identical = all(_same_state(a.state(), b.state()) for a, b in zip(together, alone))
+    pairs = sum(b["two_opt_pairs"] - a["two_opt_pairs"] for a, b in zip(st0, st1))
+    value = S_total * args.steps / (ms_batch / 1e3)
+    solo_value = S_total * args.steps / (ms_solo / 1e3)
+    batch.close()
+    for sw in together + alone:
+        sw.close()
+    ns = [i.n for i in insts]
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms_batch / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
+        "config": {"workload": f"batched-{len(insts)}", "instances": len(insts),
+                   "n_min": min(ns), "n_max": max(ns), "swarm_total": S_total,
+                   "l2": "flushed between timed generations (256 MiB write)"},
+        "batched": {"one_per_launch_value": solo_value, "speedup": value / solo_value,
+                    "one_per_launch_ms_per_step": ms_solo / args.steps,
+                    "identical_states": identical, "two_opt_rows": rows,
+                    "two_opt_pairs_per_s_over_step": pairs / (ms_batch / 1e3)},
+        "gpu_launches": None, "roofline": None, "cpu_baseline": None, "e2e": None,
+        "clocks": sampler.summary(),
+    }
+
+
+def serving_line(args):
+    """A Poisson stream of re-planning requests served by dpso_server_* with
+    continuous batching, against the same requests solved one at a time
+    (dpso_plan); tours must be identical."""
+    import numpy as np
+    import torch
+
+    from paper_1706_04399_gb300 import dpso, inputs
+
+    torch.cuda.set_device(0)
+    # the stream's requests with at most --max-n viewpoints, arrival times kept
+    full = inputs.serving()
+    stream_reqs = [r for r in full if r[1].n <= args.max_n][: args.requests]
+    cp = dpso.default_cost_params()
+    params = [dpso.default_params(swarm=inst.swarm) for _, inst in stream_reqs]
+    # one request alone first: loads the kernels so neither arm pays for it
+    _, w = stream_reqs[0]
+    dpso.dpso_plan(w.xyz, w.boxes, w.tags, cp, params[0], w.seed, 1)
+
+    server = dpso.Server(dpso.default_server_params())
+    sampler = ClockSampler(gpu_index_for_smi(0))
+    ids = []
+    with sampler:
+        t0 = time.perf_counter()
+        for (arrival, inst), p in zip(stream_reqs, params):
+            delay = arrival - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(server.submit(inst.xyz, inst.boxes, inst.tags, cp, p, inst.seed,
+                                     inst.iterations))
+        results = []
+        for rid in ids:
+            if server.wait(rid, 3600.0) != 1:
+                raise RuntimeError(f"request {rid} failed: {server.poll(rid)[0]}")
+            results.append(server.poll(rid))
+        served_s = time.perf_counter() - t0
+    sstats = server.stats()
+    server.close()
+    lat = np.array([r[3] for r in results])
+
+    t1 = time.perf_counter()
+    solo = [dpso.dpso_plan(inst.xyz, inst.boxes, inst.tags, cp, p, inst.seed, inst.iterations)
+            for (_, inst), p in zip(stream_reqs, params)]
+    solo_s = time.perf_counter() - t1
+    identical = all(r[2] == c and np.array_equal(r[1], t) for r, (t, c) in zip(results, solo))
+    units = sum(inst.swarm * inst.iterations for _, inst in stream_reqs)
+    ns = [inst.n for _, inst in stream_reqs]
+    rate = len(stream_reqs) / stream_reqs[-1][0]
+    return {
+        "metric": METRIC, "value": units / served_s, "unit": UNIT, "n_gpus": 1,
+        "steps": len(stream_reqs), "warmup": 1, "ms_per_step": 1000 * served_s / len(stream_reqs),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+        "data": "synthetic",
+        "config": {"workload": f"serving-{len(stream_reqs)}req-n{args.max_n}",
+                   "requests": len(stream_reqs), "offered_rate_hz": rate,
+                   "stream": f"first {len(stream_reqs)} requests with n <= {args.max_n} of the "
+                             f"{len(full)}-request Poisson stream (200 req/s, n log-uniform "
+                             "50..3000), arrival times kept",
+                   "n_min": min(ns), "n_max": max(ns),
+                   "swarm": stream_reqs[0][1].swarm, "iterations": stream_reqs[0][1].iterations,
+                   "l2": "inputs per request exceed L2 in aggregate; no flush"},
+        "serving": {"requests_per_s": len(stream_reqs) / served_s,
+                    "p50_latency_s": float(np.percentile(lat, 50)),
+                    "p99_latency_s": float(np.percentile(lat, 99)),
+                    "max_latency_s": float(lat.max()),
+                    "one_per_launch_requests_per_s": len(stream_reqs) / solo_s,
+                    "speedup": solo_s / served_s, "identical_tours": identical,
+                    "peak_active": sstats["peak_active"], "ticks": sstats["ticks"]},
+        "gpu_launches": None, "roofline": None, "cpu_baseline": None,
+        "e2e": {"value": units / served_s, "unit": UNIT,
+                "h2d_bytes_per_step": int(np.mean([i.xyz.nbytes + i.boxes.nbytes + i.tags.nbytes
+                                                   for _, i in stream_reqs])),
+                "d2h_bytes_per_step": int(np.mean([4 * i.n + 8 for _, i in stream_reqs])),
+                "what": "requests submitted from host buffers, tours read back; a step is one "
+                        "request"},
+        "clocks": sampler.summary(),
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="facade", choices=["tiny", "facade", "bridge"])
+    ap.add_argument("--workload", default="facade",
+                    choices=["tiny", "facade", "bridge", "batched", "serving"])
+    ap.add_argument("--instances", type=int, default=256, help="batched: instances")
+    ap.add_argument("--requests", type=int, default=48, help="serving: requests")
+    ap.add_argument("--max-n", type=int, default=400, help="serving: largest request taken")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
@@ -364,7 +538,12 @@ def main(argv=None):
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":
         return run_reference(args)
-    out = gpu_line(args)
+    if args.workload == "batched":
+        out = batched_line(args)
+    elif args.workload == "serving":
+        out = serving_line(args)
+    else:
+        out = gpu_line(args)
     if out is not None:
         print(json.dumps(out))
     return 0

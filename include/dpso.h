@@ -275,6 +275,79 @@ int dpso_plan(const double *xyz_host, int32_t n, const double *boxes_host, int32
               uint64_t seed, int32_t iterations, int32_t *tour_host, int64_t *cost);
 
 /*
+ * Re-planning server (the on-line re-planning requirement of Sec. 1 served
+ * for many requests at once; the paper has no server of its own).
+ *
+ * One engine thread per server, with its own CUDA stream on the device that
+ * is current at creation.  Requests are copied at submission and queued in
+ * arrival order.  Each engine tick admits queued requests while fewer than
+ * `max_active` are running and their estimated device footprint fits in
+ * `memory_budget_bytes` (cost matrix by dpso_cost_matrix, swarm by
+ * dpso_init; the state then stays on the device until the request ends),
+ * groups every running request into one batch (dpso_batch_*) and advances it
+ * by the smallest remaining generation budget, at most
+ * `generations_per_tick` generations.  No request runs past its own budget,
+ * so each result (tour and cost) is bit-identical to dpso_plan of the same
+ * request alone, whatever else is in the mix.  Finished requests leave the
+ * batch at the next tick and release their memory.
+ */
+typedef struct dpso_server dpso_server;
+
+typedef struct {
+    uint64_t memory_budget_bytes; /* 0: half of the free device memory at creation */
+    int32_t max_active;           /* running requests at most (default 64) */
+    int32_t generations_per_tick; /* generations per engine tick at most (default 8) */
+} dpso_server_params;
+
+typedef struct {
+    const double *xyz_host;   /* n x 3 viewpoints (m); copied at submission */
+    const double *boxes_host; /* m x 6 boxes (lo xyz, hi xyz), or NULL when m == 0 */
+    const int32_t *tags_host; /* n x 3 grid tags, or NULL */
+    int32_t n, m;
+    int32_t iterations; /* generation budget, >= 0 */
+    int32_t reserved;   /* must be 0 */
+    uint64_t seed;
+    dpso_cost_params cost;
+    dpso_params params;
+} dpso_request;
+
+typedef struct {
+    int64_t submitted, completed, failed;
+    int64_t ticks;               /* batch launches of the engine */
+    int64_t particle_iterations; /* swarm x budget summed over completed requests */
+    uint64_t memory_used_bytes;  /* footprint of the admitted requests now */
+    int32_t peak_active;         /* most requests advanced in one tick */
+    int32_t queued;              /* submitted and not yet admitted */
+    double elapsed_s;            /* since creation */
+} dpso_server_stats;
+
+void dpso_default_server_params(dpso_server_params *p);
+/* Starts the engine.  Errors: DPSO_ERR_ARG, DPSO_ERR_CUDA. */
+int dpso_server_create(dpso_server **out, const dpso_server_params *p);
+/* Queues a request (host buffers copied; the caller may free them at once)
+ * and returns its id (> 0).  Does not block on the device.  Errors:
+ * DPSO_ERR_ARG (bad sizes or parameters), DPSO_ERR_RANGE (n > DPSO_MAX_N). */
+int dpso_server_submit(dpso_server *s, const dpso_request *r, int64_t *id);
+/* The device bytes admission charges for a request (host only, no device
+ * needed): the swarm arrays dpso_init allocates for its n, swarm size,
+ * generation budget and flags, plus the transient cost-matrix buffers. */
+int dpso_server_footprint(const dpso_request *r, uint64_t *bytes);
+/* *state: 0 queued or running, 1 done, or the negative status the request
+ * failed with (DPSO_ERR_NO_MEMORY when its footprint exceeds the whole
+ * budget).  When done, copies the best tour (tour_cap >= n, tour_host may be
+ * NULL) and its cost; *latency_s (may be NULL) is the time from submission
+ * to completion.  Errors: DPSO_ERR_ARG (unknown id, tour_cap < n). */
+int dpso_server_poll(dpso_server *s, int64_t id, int32_t *state, int32_t *tour_host,
+                     int32_t tour_cap, int64_t *cost, double *latency_s);
+/* Blocks until the request leaves state 0 or timeout_s passes
+ * (DPSO_ERR_TIMEOUT); *state as in dpso_server_poll. */
+int dpso_server_wait(dpso_server *s, int64_t id, double timeout_s, int32_t *state);
+int dpso_server_stats_get(dpso_server *s, dpso_server_stats *out);
+/* Stops the engine after its current tick, frees every request's device
+ * memory and the server.  Requests not yet done are dropped.  NULL ignored. */
+void dpso_server_destroy(dpso_server *s);
+
+/*
  * Philox4x32-10 draws as the solver takes them (counter = (draw/4, particle,
  * iteration, phase), key = the seed's two 32-bit halves, word draw%4), for
  * `count` consecutive draws starting at draw 0: out_dev[d] for d < count.

@@ -32,6 +32,7 @@ SOURCES = {
     "runtime.cu": [],
     "two_opt_noalloc.cu": [],
     "probe.cu": [],
+    "server.cu": [],
 }
 
 

@@ -211,5 +211,6 @@ cudaError_t launch_two_opt_general(const TwoOptBatch& b, int num_sms, cudaStream
 // ---- runtime.cu ----
 __global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err);
 int two_opt_rows(int n);
+int validate_params(const dpso_params* p);
 
 }  // namespace dpso

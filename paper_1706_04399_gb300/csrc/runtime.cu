@@ -11,6 +11,23 @@
 
 #include "common.cuh"
 
+namespace dpso {
+
+// Parameter ranges every entry point that takes dpso_params accepts.
+int validate_params(const dpso_params* p) {
+    if (!p) return DPSO_ERR_ARG;
+    auto unit = [](double v) { return isfinite(v) && v >= 0.0 && v <= 1.0; };
+    if (!unit(p->w) || !unit(p->phi1) || !unit(p->phi2)) return DPSO_ERR_ARG;
+    if (p->swarm < 1 || p->mut_period < 1 || p->mut_swaps < 0 || p->det_frac_pct < 0 ||
+        p->det_frac_pct > 100 || p->stall_limit < 0 || p->max_moves < 0 ||
+        p->two_opt_trigger < 0 || p->two_opt_trigger > 1 || (p->flags & ~7) != 0)
+        return DPSO_ERR_ARG;
+    if (p->swarm > DPSO_MAX_SWARM) return DPSO_ERR_RANGE;
+    return DPSO_OK;
+}
+
+}  // namespace dpso
+
 using namespace dpso;
 
 namespace {
@@ -33,18 +50,6 @@ struct DeviceGuard {
 };
 
 unsigned long long q32(double c) { return static_cast<unsigned long long>(llround(ldexp(c, 32))); }
-
-int validate_params(const dpso_params* p) {
-    if (!p) return DPSO_ERR_ARG;
-    auto unit = [](double v) { return isfinite(v) && v >= 0.0 && v <= 1.0; };
-    if (!unit(p->w) || !unit(p->phi1) || !unit(p->phi2)) return DPSO_ERR_ARG;
-    if (p->swarm < 1 || p->mut_period < 1 || p->mut_swaps < 0 || p->det_frac_pct < 0 ||
-        p->det_frac_pct > 100 || p->stall_limit < 0 || p->max_moves < 0 ||
-        p->two_opt_trigger < 0 || p->two_opt_trigger > 1 || (p->flags & ~7) != 0)
-        return DPSO_ERR_ARG;
-    if (p->swarm > DPSO_MAX_SWARM) return DPSO_ERR_RANGE;
-    return DPSO_OK;
-}
 
 constexpr uint32_t kStateMagic = 0x4f535044u;  // "DPSO"
 constexpr uint32_t kStateVersion = 1;
@@ -112,14 +117,17 @@ void free_swarm(dpso_swarm* s) {
     delete s;
 }
 
+// Allocates and zero-fills on `st`, so the fill is ordered before later work
+// on that stream (a plain cudaMemset runs on the legacy stream, which
+// non-blocking streams do not wait for).
 template <typename T>
-int dalloc(T** p, size_t count) {
+int dalloc(T** p, size_t count, cudaStream_t st) {
     if (cudaMalloc(reinterpret_cast<void**>(p), count * sizeof(T)) != cudaSuccess) {
         cudaGetLastError();
         *p = nullptr;
         return DPSO_ERR_NO_MEMORY;
     }
-    if (cudaMemset(*p, 0, count * sizeof(T)) != cudaSuccess) return DPSO_ERR_CUDA;
+    if (cudaMemsetAsync(*p, 0, count * sizeof(T), st) != cudaSuccess) return DPSO_ERR_CUDA;
     return DPSO_OK;
 }
 
@@ -251,13 +259,16 @@ int ensure_history(dpso_swarm* s, int need) {
     int cap = std::max(1024, s->hist_cap);
     while (cap < need) cap *= 2;
     long long* nh = nullptr;
-    int st = dalloc(&nh, static_cast<size_t>(cap));
+    int st = dalloc(&nh, static_cast<size_t>(cap), s->last);
     if (st) return st;
-    CK(cudaStreamSynchronize(s->last));
+    // after the generations already enqueued on the swarm's stream, before
+    // the ones the caller enqueues next
     if (s->hist_cap > 0)
-        CK(cudaMemcpy(nh, s->hist, sizeof(long long) * s->hist_cap, cudaMemcpyDeviceToDevice));
-    CK(cudaMemcpy(&s->ctl->hist, &nh, sizeof(nh), cudaMemcpyHostToDevice));
-    CK(cudaMemcpy(&s->ctl->hist_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice));
+        CK(cudaMemcpyAsync(nh, s->hist, sizeof(long long) * s->hist_cap, cudaMemcpyDeviceToDevice,
+                           s->last));
+    CK(cudaMemcpyAsync(&s->ctl->hist, &nh, sizeof(nh), cudaMemcpyHostToDevice, s->last));
+    CK(cudaMemcpyAsync(&s->ctl->hist_cap, &cap, sizeof(cap), cudaMemcpyHostToDevice, s->last));
+    CK(cudaStreamSynchronize(s->last));
     cudaFree(s->hist);
     s->hist = nh;
     s->hist_cap = cap;
@@ -486,22 +497,21 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
     k.seed = seed;
     const size_t S = static_cast<size_t>(k.S), ldn = static_cast<size_t>(k.ldn);
 
-    if ((st = dalloc(&s->C, static_cast<size_t>(n) * k.ldc)) || (st = dalloc(&s->X, S * ldn)) ||
-        (st = dalloc(&s->V, S * ldn)) || (st = dalloc(&s->P, S * ldn)) ||
-        (st = dalloc(&s->G, ldn)) || (st = dalloc(&s->F, S)) || (st = dalloc(&s->PF, S)) ||
-        (st = dalloc(&s->hash, S)) || (st = dalloc(&s->dup, S)) || (st = dalloc(&s->kept, S)) ||
-        (st = dalloc(&s->ctl, 1)) || (st = dalloc(&s->meta, 1)))
+    if ((st = dalloc(&s->C, static_cast<size_t>(n) * k.ldc, ust)) ||
+        (st = dalloc(&s->X, S * ldn, ust)) || (st = dalloc(&s->V, S * ldn, ust)) ||
+        (st = dalloc(&s->P, S * ldn, ust)) || (st = dalloc(&s->G, ldn, ust)) ||
+        (st = dalloc(&s->F, S, ust)) || (st = dalloc(&s->PF, S, ust)) ||
+        (st = dalloc(&s->hash, S, ust)) || (st = dalloc(&s->dup, S, ust)) ||
+        (st = dalloc(&s->kept, S, ust)) || (st = dalloc(&s->ctl, 1, ust)) ||
+        (st = dalloc(&s->meta, 1, ust)))
         return fail(st);
     if ((st = ensure_history(s, 1024))) return fail(st);
-    // the zero-fills above ran on the legacy stream; the caller's stream may
-    // be non-blocking, so finish them before enqueuing on it
-    if (cudaDeviceSynchronize() != cudaSuccess) return fail(DPSO_ERR_CUDA);
     s->d = SwarmDev{s->C, s->X, s->V, s->P, s->G, s->F, s->PF, s->hash, s->dup, s->kept, s->ctl};
 
     int* err = nullptr;
     uint16_t* orders = nullptr;
     int* tags_dev = nullptr;
-    if ((st = dalloc(&err, 1))) return fail(st);
+    if ((st = dalloc(&err, 1, ust))) return fail(st);
     auto fail2 = [&](int code) {
         cudaFree(err);
         cudaFree(orders);
@@ -515,7 +525,8 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
     if (det) {
         s->n_det = static_cast<int>((static_cast<long long>(k.S) * p->det_frac_pct) / 100);
         s->n_det = std::min(k.S, std::max(1, s->n_det));
-        if ((st = dalloc(&orders, 8 * ldn)) || (st = dalloc(&tags_dev, 3 * static_cast<size_t>(n))))
+        if ((st = dalloc(&orders, 8 * ldn, ust)) ||
+            (st = dalloc(&tags_dev, 3 * static_cast<size_t>(n), ust)))
             return fail2(st);
         if (cudaMemcpyAsync(tags_dev, tags_host, sizeof(int) * 3 * n, cudaMemcpyHostToDevice, ust) !=
                 cudaSuccess ||
@@ -529,7 +540,8 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
     if (herr & 1) return fail2(DPSO_ERR_ARG);
     if (herr & 2) return fail2(DPSO_ERR_RANGE);
     if ((p->flags & DPSO_FLAG_TWO_OPT) && two_opt_tiled_rows(n) > 0) {
-        if ((st = dalloc(&s->Cs, static_cast<size_t>(4) * n * shifted_ld(n)))) return fail2(st);
+        if ((st = dalloc(&s->Cs, static_cast<size_t>(4) * n * shifted_ld(n), ust)))
+            return fail2(st);
         if (build_shifted_copies(s->C, k.ldc, n, s->Cs, ust) != cudaSuccess)
             return fail2(DPSO_ERR_CUDA);
     }
@@ -720,6 +732,9 @@ int dpso_set_state(dpso_swarm* s, const void* buf, size_t bytes) {
     c.moves = h.moves;
     c.runs = h.runs;
     CK(cudaMemcpy(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
+    // copies from pageable memory may return before their transfer lands;
+    // finish them before the caller's (possibly non-blocking) stream runs on
+    CK(cudaDeviceSynchronize());
     s->t_host = h.t;
     return DPSO_OK;
 }
@@ -855,10 +870,11 @@ int dpso_batch_create(dpso_batch** out, dpso_swarm* const* swarms, int32_t count
     }
     int st = DPSO_OK;
     const int nt = static_cast<int>(tasks.size());
-    if ((st = dalloc(&b->desc, count)) || (st = dalloc(&b->off, count + 1)) ||
-        (st = dalloc(&b->tasks, std::max(nt, 1))) || (st = dalloc(&b->toff, nt + 1)) ||
-        (st = dalloc(&b->queue, 1)))
+    if ((st = dalloc(&b->desc, count, b->last)) || (st = dalloc(&b->off, count + 1, b->last)) ||
+        (st = dalloc(&b->tasks, std::max(nt, 1), b->last)) ||
+        (st = dalloc(&b->toff, nt + 1, b->last)) || (st = dalloc(&b->queue, 1, b->last)))
         return fail(st);
+    if (cudaStreamSynchronize(b->last) != cudaSuccess) return fail(DPSO_ERR_CUDA);
     if (cudaMemcpy(b->desc, desc.data(), sizeof(SwarmDesc) * count, cudaMemcpyHostToDevice) !=
             cudaSuccess ||
         cudaMemcpy(b->off, off.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice) !=
@@ -921,9 +937,9 @@ int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, void* stream) {
             long long* cost = nullptr;
             unsigned long long* cnt = nullptr;
             int* status = nullptr;
-            if ((st2 = dalloc(&tours, static_cast<size_t>(t.count) * t.ldt)) ||
-                (st2 = dalloc(&cost, t.count)) || (st2 = dalloc(&cnt, 2)) ||
-                (st2 = dalloc(&status, 1)))
+            if ((st2 = dalloc(&tours, static_cast<size_t>(t.count) * t.ldt, st)) ||
+                (st2 = dalloc(&cost, t.count, st)) || (st2 = dalloc(&cnt, 2, st)) ||
+                (st2 = dalloc(&status, 1, st)))
                 break;
             scratch.insert(scratch.end(), {tours, cost, cnt, status});
             t.tours = tours;
@@ -936,9 +952,10 @@ int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, void* stream) {
             t.status = status;
         }
         TwoOptTask* dtasks = nullptr;
-        if (!st2 && !(st2 = dalloc(&dtasks, tasks.size()))) {
-            CK(cudaMemcpy(dtasks, tasks.data(), sizeof(TwoOptTask) * tasks.size(),
-                          cudaMemcpyHostToDevice));
+        if (!st2 && !(st2 = dalloc(&dtasks, tasks.size(), st))) {
+            CK(cudaMemcpyAsync(dtasks, tasks.data(), sizeof(TwoOptTask) * tasks.size(),
+                               cudaMemcpyHostToDevice, st));
+            CK(cudaStreamSynchronize(st));
             cudaEvent_t e0, e1;
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));

@@ -66,6 +66,26 @@ class dpso_timing(ctypes.Structure):
                 ("generations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class dpso_server_params(ctypes.Structure):
+    _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_int32),
+                ("generations_per_tick", ctypes.c_int32)]
+
+
+class dpso_request(ctypes.Structure):
+    _fields_ = [("xyz_host", ctypes.c_void_p), ("boxes_host", ctypes.c_void_p),
+                ("tags_host", ctypes.c_void_p), ("n", ctypes.c_int32), ("m", ctypes.c_int32),
+                ("iterations", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("cost", dpso_cost_params), ("params", dpso_params)]
+
+
+class dpso_server_stats(ctypes.Structure):
+    _fields_ = [("submitted", ctypes.c_int64), ("completed", ctypes.c_int64),
+                ("failed", ctypes.c_int64), ("ticks", ctypes.c_int64),
+                ("particle_iterations", ctypes.c_int64), ("memory_used_bytes", ctypes.c_uint64),
+                ("peak_active", ctypes.c_int32), ("queued", ctypes.c_int32),
+                ("elapsed_s", ctypes.c_double)]
+
+
 _lib = None
 _vp = ctypes.c_void_p
 _i32 = ctypes.c_int32
@@ -117,6 +137,17 @@ def lib():
             "dpso_batch_destroy": (None, [_vp]),
             "dpso_probe_l2_read_gbs": (ctypes.c_int, [ctypes.c_size_t, _i32,
                                                       ctypes.POINTER(ctypes.c_double), _vp]),
+            "dpso_default_server_params": (None, [ctypes.POINTER(dpso_server_params)]),
+            "dpso_server_create": (ctypes.c_int, [ctypes.POINTER(_vp),
+                                                  ctypes.POINTER(dpso_server_params)]),
+            "dpso_server_submit": (ctypes.c_int, [_vp, ctypes.POINTER(dpso_request), _i64p]),
+            "dpso_server_footprint": (ctypes.c_int, [ctypes.POINTER(dpso_request),
+                                                     ctypes.POINTER(ctypes.c_uint64)]),
+            "dpso_server_poll": (ctypes.c_int, [_vp, ctypes.c_int64, _i32p, _i32p, _i32, _i64p,
+                                                ctypes.POINTER(ctypes.c_double)]),
+            "dpso_server_wait": (ctypes.c_int, [_vp, ctypes.c_int64, ctypes.c_double, _i32p]),
+            "dpso_server_stats_get": (ctypes.c_int, [_vp, ctypes.POINTER(dpso_server_stats)]),
+            "dpso_server_destroy": (None, [_vp]),
             "dpso_philox_draws": (ctypes.c_int, [ctypes.c_uint64, ctypes.c_uint32,
                                                  ctypes.c_uint32, ctypes.c_uint32, _i32, _vp, _vp]),
         }
@@ -350,6 +381,93 @@ class Batch:
     def close(self):
         if getattr(self, "_h", None) and self._h.value:
             lib().dpso_batch_destroy(self._h)
+            self._h = _vp()
+
+    __del__ = close
+
+
+def default_server_params(**overrides) -> dpso_server_params:
+    p = dpso_server_params()
+    lib().dpso_default_server_params(ctypes.byref(p))
+    for k, v in overrides.items():
+        setattr(p, k, v)
+    return p
+
+
+def make_request(xyz: np.ndarray, boxes: np.ndarray, tags, cp: dpso_cost_params,
+                 p: dpso_params, seed: int, iterations: int):
+    """A dpso_request and the contiguous arrays it points into (keep them alive)."""
+    xyz = np.ascontiguousarray(xyz, dtype=np.float64)
+    boxes = np.ascontiguousarray(boxes, dtype=np.float64).reshape(-1, 6)
+    tg = None if tags is None else np.ascontiguousarray(tags, dtype=np.int32)
+    r = dpso_request()
+    r.xyz_host = xyz.ctypes.data
+    r.boxes_host = boxes.ctypes.data if boxes.shape[0] else None
+    r.tags_host = None if tg is None else tg.ctypes.data
+    r.n, r.m = xyz.shape[0], boxes.shape[0]
+    r.iterations = iterations
+    r.seed = seed
+    r.cost = cp
+    r.params = p
+    return r, (xyz, boxes, tg)
+
+
+def dpso_server_footprint(xyz, boxes, tags, cp, p, seed, iterations) -> int:
+    r, _keep = make_request(xyz, boxes, tags, cp, p, seed, iterations)
+    out = ctypes.c_uint64(0)
+    _check(lib().dpso_server_footprint(ctypes.byref(r), ctypes.byref(out)),
+           "dpso_server_footprint")
+    return out.value
+
+
+class Server:
+    """Owns a dpso_server: submit / poll / wait / stats / close."""
+
+    def __init__(self, params: dpso_server_params | None = None):
+        p = params if params is not None else default_server_params()
+        h = _vp()
+        _check(lib().dpso_server_create(ctypes.byref(h), ctypes.byref(p)), "dpso_server_create")
+        self._h = h
+        self._n = {}
+
+    def submit(self, xyz: np.ndarray, boxes: np.ndarray, tags, cp: dpso_cost_params,
+               p: dpso_params, seed: int, iterations: int) -> int:
+        r, keep = make_request(xyz, boxes, tags, cp, p, seed, iterations)
+        rid = ctypes.c_int64(0)
+        _check(lib().dpso_server_submit(self._h, ctypes.byref(r), ctypes.byref(rid)),
+               "dpso_server_submit")
+        self._n[rid.value] = keep[0].shape[0]
+        return rid.value
+
+    def poll(self, rid: int):
+        """(state, tour or None, cost or None, latency_s); state 0 pending, 1 done, < 0 failed."""
+        n = self._n.get(rid, 0)
+        tour = np.zeros(max(n, 1), np.int32)
+        state = ctypes.c_int32(0)
+        cost = ctypes.c_int64(0)
+        lat = ctypes.c_double(0.0)
+        _check(lib().dpso_server_poll(self._h, rid, ctypes.byref(state),
+                                      tour.ctypes.data_as(_i32p), n, ctypes.byref(cost),
+                                      ctypes.byref(lat)), "dpso_server_poll")
+        if state.value == 1:
+            return 1, tour, cost.value, lat.value
+        return state.value, None, None, lat.value
+
+    def wait(self, rid: int, timeout_s: float = 600.0) -> int:
+        state = ctypes.c_int32(0)
+        st = lib().dpso_server_wait(self._h, rid, timeout_s, ctypes.byref(state))
+        if st not in (OK, ERR_TIMEOUT):
+            _check(st, "dpso_server_wait")
+        return state.value
+
+    def stats(self) -> dict:
+        st = dpso_server_stats()
+        _check(lib().dpso_server_stats_get(self._h, ctypes.byref(st)), "dpso_server_stats_get")
+        return {k: getattr(st, k) for k, _ in dpso_server_stats._fields_}
+
+    def close(self):
+        if getattr(self, "_h", None) and self._h.value:
+            lib().dpso_server_destroy(self._h)
             self._h = _vp()
 
     __del__ = close

@@ -57,3 +57,40 @@ def test_argument_errors_need_no_device(libpath):
     ok = dpso.default_params()
     assert L.dpso_init(ctypes.byref(h), 1, dpso.MAX_N + 1, None, ctypes.byref(ok), 1,
                        None) == dpso.ERR_RANGE
+
+
+def test_server_host_side_checks(libpath):
+    from paper_1706_04399_gb300 import dpso, inputs
+    L = dpso.lib()
+    sp = dpso.default_server_params()
+    assert (sp.memory_budget_bytes, sp.max_active, sp.generations_per_tick) == (0, 64, 8)
+    h = ctypes.c_void_p()
+    for bad in (dpso.default_server_params(max_active=0),
+                dpso.default_server_params(generations_per_tick=0)):
+        assert L.dpso_server_create(ctypes.byref(h), ctypes.byref(bad)) == dpso.ERR_ARG
+    state = ctypes.c_int32(0)
+    assert L.dpso_server_poll(None, 1, ctypes.byref(state), None, 0, None, None) == dpso.ERR_ARG
+    assert L.dpso_server_wait(None, 1, 0.0, ctypes.byref(state)) == dpso.ERR_ARG
+    L.dpso_server_destroy(None)
+
+    # admission footprint: grows with n, swarm and budget; the 2-opt copies count
+    inst = inputs.random_instance(200, 3, 1)
+    cp = dpso.default_cost_params()
+
+    def fp(n_inst, **kw):
+        p = dpso.default_params(swarm=kw.pop("swarm", 64))
+        for k, v in kw.items():
+            setattr(p, k, v)
+        return dpso.dpso_server_footprint(n_inst.xyz, n_inst.boxes, n_inst.tags, cp, p, 1, 50)
+
+    base = fp(inst)
+    assert base >= 200 * 224 * 4 + 4 * 200 * 212 * 4 + 3 * 64 * 200 * 2
+    assert fp(inputs.random_instance(400, 3, 1)) > 3 * base
+    assert fp(inst, swarm=128) > base
+    assert fp(inst, flags=dpso.FLAG_DET_INIT) < base - 4 * 200 * 200 * 4
+    r, _keep = dpso.make_request(inst.xyz, inst.boxes, inst.tags, cp, dpso.default_params(), 1, 5)
+    r.n = 2
+    out = ctypes.c_uint64(0)
+    assert L.dpso_server_footprint(ctypes.byref(r), ctypes.byref(out)) == dpso.ERR_ARG
+    r.n = dpso.MAX_N + 1
+    assert L.dpso_server_footprint(ctypes.byref(r), ctypes.byref(out)) == dpso.ERR_RANGE

@@ -227,3 +227,30 @@ def test_full_size_two_opt_from_initial_tours(name, count, sample):
         assert np.array_equal(np.sort(got[k]), np.arange(n))
     for k in range(0, count, max(1, count // 8)):
         assert got_c[k] == oracle.fitness(C_np, got[k])
+
+
+def test_side_stream_matches_default_stream():
+    """A swarm created, stepped and checkpointed on a non-blocking stream
+    follows the same trajectory as one on the legacy default stream (every
+    zero-fill and upload of the library is ordered on the caller's stream)."""
+    inst = inputs.planar_grid(1367, 1.0, np.zeros((0, 6)), "grid1367", 96, 4, 0)
+    C = cost_matrix_gpu(inst)
+    p = dpso.default_params(swarm=inst.swarm)
+    ref = dpso.Swarm(C, inst.n, inst.tags, p, inst.seed)
+    ref.step(inst.iterations)
+    want = ref.state()
+    side = torch.cuda.Stream()
+    for _ in range(3):
+        sw = dpso.Swarm(C, inst.n, inst.tags, p, inst.seed, side)
+        sw.step(2, side)
+        blob = sw.state_bytes()
+        sw.set_state_bytes(blob)
+        sw.step(inst.iterations - 2, side)
+        got = sw.state()
+        for key in ("X", "V", "P", "G", "F", "PF", "history"):
+            assert np.array_equal(got[key], want[key]), key
+        sw.close()
+    tour, cost = dpso.dpso_plan(inst.xyz, inst.boxes, inst.tags, dpso.default_cost_params(), p,
+                                inst.seed, inst.iterations)
+    assert cost == want["gf"] and np.array_equal(tour, want["G"].astype(np.int32))
+    ref.close()

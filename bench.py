@@ -289,7 +289,9 @@ def gpu_line(args):
     out = None
     if rank == 0:
         peaks = measured_peaks()
-        l2 = dpso.dpso_probe_l2_read_gbs(24 << 20, 40)
+        probes = {f"{mb}MiB": dpso.dpso_probe_l2_read_gbs(mb << 20, max(1, 960 // mb))
+                  for mb in (8, 16, 24)}
+        l2 = max(probes.values())
         achieved = BYTES_PER_PAIR * pairs / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
         traffic = two_opt_traffic(inst.name)
         roofline = {
@@ -297,7 +299,9 @@ def gpu_line(args):
             "unit": "GB/s", "frac": achieved / l2 if l2 else None,
             "traffic": traffic,
             "peak_source": "L2 read bandwidth measured in this run by dpso_probe_l2_read_gbs "
-                           "(16-byte loads of a 24 MiB L2-resident buffer, best of 5)",
+                           "(16-byte loads of an L2-resident buffer, best of 5 runs, best of "
+                           "8/16/24 MiB buffers)",
+            "l2_probes_gbs": probes,
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
             "frac_of_hbm_peak": achieved / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
         }
@@ -388,7 +392,7 @@ def batched_line(args):
 
     together, alone = swarms(), swarms()
     batch = dpso.Batch(together, stream)
-    rows = batch.autotune(stream)
+    rows, tpc = batch.autotune(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     S_total = sum(i.swarm for i in insts)
 
@@ -434,7 +438,7 @@ def batched_line(args):
                    "l2": "flushed between timed generations (256 MiB write)"},
         "batched": {"one_per_launch_value": solo_value, "speedup": value / solo_value,
                     "one_per_launch_ms_per_step": ms_solo / args.steps,
-                    "identical_states": identical, "two_opt_rows": rows,
+                    "identical_states": identical, "two_opt_rows": rows, "two_opt_tours_per_cta": tpc,
                     "two_opt_pairs_per_s_over_step": pairs / (ms_batch / 1e3)},
         "gpu_launches": None, "roofline": None, "cpu_baseline": None, "e2e": None,
         "clocks": sampler.summary(),

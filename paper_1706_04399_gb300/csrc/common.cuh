@@ -197,6 +197,7 @@ struct TwoOptBatch {
     bool shifted;     // every task has Cs: the tiled kernel may be used
     int rows;         // tile height of the tiled kernel (0: the default for max_n)
     unsigned int* queue;
+    int tpc;          // tours per CTA of the tiled kernel (0: the default for max_n)
 };
 cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 
@@ -204,8 +205,11 @@ cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 __host__ __device__ int shifted_ld(int n);
 size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages);
 int two_opt_tiled_rows(int n);  // default tile height, 0 when no height fits
+int two_opt_tiled_tpc(int n, int rows);  // default tours per CTA
+bool two_opt_tiled_fits(int n, int rows, int tpc);  // the shape's shared memory fits
 cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStream_t st);
-cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int num_sms, cudaStream_t st);
+cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int tpc, int num_sms,
+                                 cudaStream_t st);
 cudaError_t launch_two_opt_general(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 
 // ---- runtime.cu ----

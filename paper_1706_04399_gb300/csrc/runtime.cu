@@ -917,19 +917,23 @@ int dpso_batch_step(dpso_batch* b, int32_t iterations, void* stream) {
     return DPSO_OK;
 }
 
-int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, void* stream) {
+int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, int32_t* tpc_out, void* stream) {
     if (!b) return DPSO_ERR_ARG;
     DeviceGuard g(b->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaStreamSynchronize(b->last));
     b->last = st;
-    int chosen = 0;
+    int chosen_rows = 0, chosen_tpc = 0;
     if (b->tb.nprob > 0 && b->tb.shifted && two_opt_tiled_rows(b->tb.max_n) > 0) {
-        // Time each tile height on scratch copies of every member's current
-        // tours, with the gates ignored; the choice cannot change results.
+        // Time every (tile height, tours per CTA) that fits on scratch copies
+        // of the members' current tours, the gates ignored and at most
+        // kProbeMoves moves per tour (a fixed amount of work per candidate);
+        // the choice cannot change results.
+        constexpr int kProbeMoves = 8;
         std::vector<TwoOptTask> tasks(b->tb.nprob);
         CK(cudaMemcpy(tasks.data(), b->tasks, sizeof(TwoOptTask) * b->tb.nprob,
                       cudaMemcpyDeviceToHost));
+        const std::vector<TwoOptTask> orig = tasks;
         std::vector<void*> scratch;
         int st2 = DPSO_OK;
         for (TwoOptTask& t : tasks) {
@@ -950,6 +954,7 @@ int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, void* stream) {
             t.pairs = cnt;
             t.moves = cnt + 1;
             t.status = status;
+            t.max_moves = kProbeMoves;
         }
         TwoOptTask* dtasks = nullptr;
         if (!st2 && !(st2 = dalloc(&dtasks, tasks.size(), st))) {
@@ -961,33 +966,35 @@ int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, void* stream) {
             CK(cudaEventCreate(&e1));
             float best = 1e30f;
             for (int rows : {32, 24, 16, 8}) {
-                if (two_opt_tiled_smem(b->tb.max_n, rows, 1) > 220 * 1024) continue;
-                // restore the tours, then time one exchange
-                std::vector<TwoOptTask> orig(b->tb.nprob);
-                CK(cudaMemcpy(orig.data(), b->tasks, sizeof(TwoOptTask) * b->tb.nprob,
-                              cudaMemcpyDeviceToHost));
-                for (size_t i = 0; i < tasks.size(); ++i) {
-                    CK(cudaMemcpy2DAsync(tasks[i].tours, sizeof(uint16_t) * tasks[i].ldt,
-                                         orig[i].tours, sizeof(uint16_t) * orig[i].ldt,
-                                         sizeof(uint16_t) * tasks[i].n, tasks[i].count,
-                                         cudaMemcpyDeviceToDevice, st));
-                    CK(cudaMemcpyAsync(tasks[i].cost, orig[i].cost,
-                                       sizeof(long long) * tasks[i].count,
-                                       cudaMemcpyDeviceToDevice, st));
-                }
-                TwoOptBatch tb = b->tb;
-                tb.tasks = dtasks;
-                tb.rows = rows;
-                CK(cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st));
-                CK(cudaEventRecord(e0, st));
-                CK(launch_two_opt_tiled(tb, rows, b->num_sms, st));
-                CK(cudaEventRecord(e1, st));
-                CK(cudaEventSynchronize(e1));
-                float ms = 0.f;
-                CK(cudaEventElapsedTime(&ms, e0, e1));
-                if (ms < best) {
-                    best = ms;
-                    chosen = rows;
+                for (int tpc : {1, 2, 4}) {
+                    for (size_t i = 0; i < tasks.size(); ++i) {  // restore the tours
+                        CK(cudaMemcpy2DAsync(tasks[i].tours, sizeof(uint16_t) * tasks[i].ldt,
+                                             orig[i].tours, sizeof(uint16_t) * orig[i].ldt,
+                                             sizeof(uint16_t) * tasks[i].n, tasks[i].count,
+                                             cudaMemcpyDeviceToDevice, st));
+                        CK(cudaMemcpyAsync(tasks[i].cost, orig[i].cost,
+                                           sizeof(long long) * tasks[i].count,
+                                           cudaMemcpyDeviceToDevice, st));
+                    }
+                    TwoOptBatch tb = b->tb;
+                    tb.tasks = dtasks;
+                    CK(cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st));
+                    CK(cudaEventRecord(e0, st));
+                    const cudaError_t le = launch_two_opt_tiled(tb, rows, tpc, b->num_sms, st);
+                    if (le == cudaErrorInvalidValue || le == cudaErrorInvalidConfiguration) {
+                        cudaGetLastError();  // this shape does not fit: skip it
+                        continue;
+                    }
+                    CK(le);
+                    CK(cudaEventRecord(e1, st));
+                    CK(cudaEventSynchronize(e1));
+                    float ms = 0.f;
+                    CK(cudaEventElapsedTime(&ms, e0, e1));
+                    if (ms < best) {
+                        best = ms;
+                        chosen_rows = rows;
+                        chosen_tpc = tpc;
+                    }
                 }
             }
             cudaEventDestroy(e0);
@@ -997,14 +1004,32 @@ int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, void* stream) {
         if (dtasks) cudaFree(dtasks);
         for (void* p : scratch) cudaFree(p);
         if (st2) return st2;
-        if (chosen > 0 && chosen != b->tb.rows) {
-            b->tb.rows = chosen;
+        if (chosen_rows > 0 && (chosen_rows != b->tb.rows || chosen_tpc != b->tb.tpc)) {
+            b->tb.rows = chosen_rows;
+            b->tb.tpc = chosen_tpc;
             const int r = capture_batch(b);
             if (r) return r;
         }
     }
-    if (rows_out) *rows_out = b->tb.rows > 0 ? b->tb.rows : two_opt_tiled_rows(b->tb.max_n);
+    const int rows = b->tb.rows > 0 ? b->tb.rows : two_opt_tiled_rows(b->tb.max_n);
+    if (rows_out) *rows_out = rows;
+    if (tpc_out) *tpc_out = b->tb.tpc > 0 ? b->tb.tpc : (rows > 0 ? two_opt_tiled_tpc(b->tb.max_n, rows) : 0);
     return DPSO_OK;
+}
+
+int dpso_batch_set_two_opt_shape(dpso_batch* b, int32_t rows, int32_t tpc) {
+    if (!b) return DPSO_ERR_ARG;
+    DeviceGuard g(b->device);
+    if (rows == 0 && tpc == 0) {  // back to the defaults for the longest tour
+        b->tb.rows = 0;
+        b->tb.tpc = 0;
+    } else {
+        if (!b->tb.shifted || !two_opt_tiled_fits(b->tb.max_n, rows, tpc)) return DPSO_ERR_ARG;
+        b->tb.rows = rows;
+        b->tb.tpc = tpc;
+    }
+    CK(cudaStreamSynchronize(b->last));
+    return capture_batch(b);
 }
 
 void dpso_batch_destroy(dpso_batch* b) {

@@ -242,9 +242,11 @@ cudaError_t launch_two_opt_general(const TwoOptBatch& b, int num_sms, cudaStream
 
 cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     if (b.total <= 0) return cudaSuccess;
-    if (b.shifted && two_opt_tiled_rows(b.max_n) > 0)
-        return launch_two_opt_tiled(b, b.rows > 0 ? b.rows : two_opt_tiled_rows(b.max_n), num_sms,
-                                    st);
+    if (b.shifted && two_opt_tiled_rows(b.max_n) > 0) {
+        const int rows = b.rows > 0 ? b.rows : two_opt_tiled_rows(b.max_n);
+        const int tpc = b.tpc > 0 ? b.tpc : two_opt_tiled_tpc(b.max_n, rows);
+        return launch_two_opt_tiled(b, rows, tpc, num_sms, st);
+    }
     return launch_two_opt_general(b, num_sms, st);
 }
 

@@ -19,10 +19,13 @@
 //  * Column records rec[c] = {x_c+1, -C[x_c][x_c+1]} give the second gather's
 //    column and the edge term in one broadcast load; the first gather's column
 //    x_c is the previous record's.
-//  * Each lane tracks, over its columns in increasing order, the first minimum
-//    of C[x_i][x_c] + C[x_i+1][x_c+1] - C[x_c][x_c+1] and the two gathered
-//    costs there.  Subtracting C[x_i][x_i+1] gives a candidate (delta, i, j);
-//    a packed 64-bit key keeps the lexicographically smallest across tiles.
+//  * Each lane tracks, over its columns in increasing order (groups of four),
+//    the minimum of C[x_i][x_c] + C[x_i+1][x_c+1] - C[x_c][x_c+1] and the
+//    first group holding it, with selects only (no divergent branch in the
+//    column loop).  Subtracting C[x_i][x_i+1] gives a candidate (delta, i,
+//    group); a packed 64-bit key keeps the lexicographically smallest across
+//    tiles, and when a tile's candidate wins, its exact column and the two
+//    gathered costs are read back from the still-staged tile.
 //    One block reduction per pass yields (delta*, i*, j*), and the winning
 //    lane publishes C[x_i*][x_j*] and C[x_i*+1][x_j*+1], the two new edges.
 //  * Pairs with j = i+1 and (0, n-1) have delta = 0 for a symmetric C and
@@ -96,48 +99,81 @@ size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages) {
 
 namespace {
 
-// Record cost of the padding columns past n: larger than any real column
-// value (at most 2^30), so padding never supplies an improving move.
-constexpr int kPadCost = (1 << 30) + 1;
+// Record term of the padding columns past n.  A padding column evaluates to
+// a + b + kPadCost with a, b <= DPSO_COST_MAX = 2^29, at most 2^31 - 1, so the
+// int32 sum cannot wrap; its delta (that minus the row's own edge, <= 2^29)
+// is at least 2^29 - 1 > 0, so padding never supplies an improving move.
+constexpr int kPadCost = (1 << 30) - 1;
+static_assert(2LL * DPSO_COST_MAX + kPadCost <= INT_MAX, "padding column overflows");
+static_assert(static_cast<long long>(kPadCost) - DPSO_COST_MAX > 0, "padding column improves");
 
-template <int ROWS, int STAGES>
-__global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) {
-    constexpr int kRows = ROWS;           // positions per tile, one per lane
-    constexpr int kStaged = ROWS + 1;     // cost rows staged per tile
-    // One dynamic shared block seen through three element types (all arrays
-    // alias its start): STAGES tile buffers of kStaged x ldq ints, then the
-    // column records (n + 4 int2, the last four padding), then the tour
-    // (n + 1 uint16).  Offsets depend on the tour's n; the block is sized for
-    // the largest n of the launch.
-    extern __shared__ __align__(128) int smi[];
-    extern __shared__ __align__(128) int2 smi2[];
-    extern __shared__ __align__(128) int4 smi4[];
-    extern __shared__ __align__(128) uint16_t smu[];
+// Barrier over the WPT warps that own one tour: the whole block when a CTA
+// holds one tour, else named barrier 1 + group (WPT * 32 threads).
+template <int TPC>
+__device__ __forceinline__ void group_sync(int grp) {
+    constexpr int kCount = kThreads / TPC;
+    if constexpr (TPC == 1) {
+        __syncthreads();
+    } else {
+        // constant barrier ids (grp is uniform per warp), so only TPC + 1 of
+        // the 16 hardware barriers are reserved
+        switch (grp) {
+            case 0: asm volatile("bar.sync 1, %0;\n" ::"n"(kCount) : "memory"); break;
+            case 1: asm volatile("bar.sync 2, %0;\n" ::"n"(kCount) : "memory"); break;
+            case 2: asm volatile("bar.sync 3, %0;\n" ::"n"(kCount) : "memory"); break;
+            default: asm volatile("bar.sync 4, %0;\n" ::"n"(kCount) : "memory"); break;
+        }
+    }
+}
+
+// ROWS: tile height (positions per tile, one per lane).  TPC: tours per CTA;
+// the 8 warps split into TPC groups of 8 / TPC warps, each solving its own
+// tour in its own slice of shared memory (`group_words` ints, 128-byte
+// aligned), so short tours still give every warp a long column range.
+template <int ROWS, int TPC>
+__global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
+    constexpr int kRows = ROWS;        // positions per tile, one per lane
+    constexpr int kStaged = ROWS + 1;  // cost rows staged per tile
+    constexpr int WPT = kWarps / TPC;  // warps per tour
+    constexpr int GT = WPT * 32;       // threads per tour
+    // A group's shared slice seen through three element types (all alias its
+    // start): the tile buffer of kStaged x ldq ints, then the column records
+    // (n + 4 int2, the last four padding), then the tour (n + 1 uint16).
+    // Offsets depend on the tour's n; slices are sized for the largest n.
+    extern __shared__ __align__(128) int sm_all[];
     __shared__ unsigned long long s_key[kWarps];
-    __shared__ unsigned long long s_best;
-    __shared__ int s_part, s_e0, s_e1;
-    __shared__ long long s_pf;
+    __shared__ unsigned long long s_best[TPC];
+    __shared__ int s_part[TPC], s_e0[TPC], s_e1[TPC];
+    __shared__ long long s_pf[TPC];
 
-    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const int lane = threadIdx.x & 31;
+    const int grp = (threadIdx.x >> 5) / WPT;  // tour group
+    const int warp = (threadIdx.x >> 5) % WPT; // warp within the group
+    const int tid = threadIdx.x % GT;          // thread within the group
+    int* smi = sm_all + static_cast<size_t>(grp) * group_words;
+    int2* smi2 = reinterpret_cast<int2*>(smi);
+    const int4* smi4 = reinterpret_cast<const int4*>(smi);
+    uint16_t* smu = reinterpret_cast<uint16_t*>(smi);
+    unsigned long long* s_keyg = s_key + grp * WPT;
 
     for (;;) {
-        if (tid == 0) s_part = static_cast<int>(atomicAdd(b.queue, 1u));
-        __syncthreads();
-        const int g = s_part;
+        if (tid == 0) s_part[grp] = static_cast<int>(atomicAdd(b.queue, 1u));
+        group_sync<TPC>(grp);
+        const int g = s_part[grp];
         if (g >= b.total) break;
         const int prob = find_inst(b.off, b.nprob, g);
         const int p = g - b.off[prob];
         const TwoOptTask a = b.tasks[prob];
         if (a.gate && *a.gate == 0) {  // this problem does not exchange edges now
-            __syncthreads();
+            group_sync<TPC>(grp);
             continue;
         }
         const int n = a.n;
         const int ldq = shifted_ld(n);
         const int q16 = ldq / 4;
         const int buf_words = kStaged * ldq;
-        const int rec2 = STAGES * buf_words / 2;  // int2 index of record 0 (even)
-        const int xs16 = (rec2 + n + 4) * 4;      // uint16 index of x_0
+        const int rec2 = buf_words / 2;         // int2 index of record 0 (even)
+        const int xs16 = (rec2 + n + 4) * 4;    // uint16 index of x_0
         const int* __restrict__ C = a.C;
         const int* __restrict__ Cs = a.Cs;
         const int ldc = a.ldc;
@@ -145,18 +181,16 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) 
         const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
         const int guard = 1000 + 100 * n;
 
-        // All threads: copy the cost rows of tile t into buffer t % STAGES.
-        auto stage = [&](int t) {
-            const int I = t * kRows;
+        // The group's threads copy the cost rows of the tile starting at I.
+        auto stage = [&](int I) {
             const int count = min(kStaged, n - 1 - I);
-            const int boff = (t % STAGES) * buf_words;
-            for (int r = warp; r < count; r += kWarps) {
+            for (int r = warp; r < count; r += WPT) {
                 const int k = (r >> 3) & 3;
                 const char* src =
                     reinterpret_cast<const char*>(
                         Cs + (static_cast<size_t>(k) * n + smu[xs16 + I + r]) * ldq) +
                     lane * 16;
-                int* dst = smi + boff + r * ldq + lane * 4;
+                int* dst = smi + r * ldq + lane * 4;
 #pragma unroll
                 for (int j = 0; j < 4; ++j)
                     if (j * 32 + lane < q16) cp_async16(dst + j * 128, src + j * 512);
@@ -165,17 +199,17 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) 
         };
 
         uint16_t* tour = a.tours + static_cast<size_t>(p) * a.ldt;
-        for (int i = tid; i < n; i += kThreads) smu[xs16 + i] = tour[i];
+        for (int i = tid; i < n; i += GT) smu[xs16 + i] = tour[i];
         if (tid == 0) smu[xs16 + n] = tour[0];
-        __syncthreads();
-        for (int c = tid; c < n; c += kThreads) {
+        group_sync<TPC>(grp);
+        for (int c = tid; c < n; c += GT) {
             const int u = smu[xs16 + c], v = smu[xs16 + c + 1];
             smi2[rec2 + c] = make_int2(v, -C[static_cast<size_t>(u) * ldc + v]);
         }
         if (tid < 4) smi2[rec2 + n + tid] = make_int2(0, kPadCost);
         long long f = a.cost[p];
         int moves = 0, passes = 0;
-        __syncthreads();
+        group_sync<TPC>(grp);
 
         for (;;) {
             if (a.max_moves > 0 && moves >= a.max_moves) break;
@@ -183,53 +217,36 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) 
                 if (tid == 0 && a.status) atomicExch(a.status, DPSO_ERR_INTERNAL);
                 break;
             }
-            if constexpr (STAGES > 1) {
-#pragma unroll
-                for (int s = 0; s < STAGES - 1; ++s) {
-                    if (s < ntiles) stage(s);
-                    cp_async_commit();
-                }
-            }
             unsigned long long key = ~0ull;
             int ke0 = 0, ke1 = 0;
             for (int t = 0; t < ntiles; ++t) {
-                if constexpr (STAGES == 1) {
-                    __syncthreads();
-                    stage(t);
-                    cp_async_commit();
-                    cp_async_wait<0>();
-                    __syncthreads();
-                } else {
-                    cp_async_wait<STAGES - 2>();
-                    __syncthreads();
-                    if (t + STAGES - 1 < ntiles) stage(t + STAGES - 1);
-                    cp_async_commit();
-                }
                 const int I = t * kRows;
-                const int boff = (t % STAGES) * buf_words;
+                group_sync<TPC>(grp);  // the previous tile is no longer read
+                stage(I);
+                cp_async_commit();
+                cp_async_wait<0>();
+                group_sync<TPC>(grp);
                 // lanes past the tile height idle on a valid row
                 const int ra = min(lane, kRows - 1), rb1 = min(lane + 1, kRows);
-                const int p1 = boff + ra * ldq + ((ra >> 3) & 3);
-                const int p2 = boff + rb1 * ldq + ((rb1 >> 3) & 3);
+                const int p1 = ra * ldq + ((ra >> 3) & 3);
+                const int p2 = rb1 * ldq + ((rb1 >> 3) & 3);
                 // columns in groups of four, contiguous per warp; the records
                 // past n are padding
                 const int cbeg = I + 2;
                 const int ngroups = (n - cbeg + 3) >> 2;
-                const int g0 = (ngroups * warp) / kWarps, g1 = (ngroups * (warp + 1)) / kWarps;
+                const int g0 = (ngroups * warp) / WPT, g1 = (ngroups * (warp + 1)) / WPT;
                 // first valid column of this lane's row (rows past n-3 have none)
                 const int lim = (lane < kRows && I + lane <= n - 3) ? I + lane + 2 : INT_MAX;
-                int m = INT_MAX, cm = 0, e0 = 0, e1 = 0;
+                int m = INT_MAX, cm = 0;
                 int c = cbeg + 4 * g0;
                 const int cend = cbeg + 4 * g1;
                 int q = g0 < g1 ? smi2[rec2 + c - 1].x : 0;  // x_c
                 auto group = [&](bool masked) {
-                    const int4 ra = smi4[(rec2 + c) >> 1], rb = smi4[(rec2 + c + 2) >> 1];
-                    const int a0 = smi[p1 + q], b0 = smi[p2 + ra.x];
-                    const int a1 = smi[p1 + ra.x], b1 = smi[p2 + ra.z];
-                    const int a2 = smi[p1 + ra.z], b2 = smi[p2 + rb.x];
-                    const int a3 = smi[p1 + rb.x], b3 = smi[p2 + rb.z];
-                    int v0 = a0 + b0 + ra.y, v1 = a1 + b1 + ra.w;
-                    int v2 = a2 + b2 + rb.y, v3 = a3 + b3 + rb.w;
+                    const int4 ra4 = smi4[(rec2 + c) >> 1], rb4 = smi4[(rec2 + c + 2) >> 1];
+                    int v0 = smi[p1 + q] + smi[p2 + ra4.x] + ra4.y;
+                    int v1 = smi[p1 + ra4.x] + smi[p2 + ra4.z] + ra4.w;
+                    int v2 = smi[p1 + ra4.z] + smi[p2 + rb4.x] + rb4.y;
+                    int v3 = smi[p1 + rb4.x] + smi[p2 + rb4.z] + rb4.w;
                     if (masked) {
                         v0 = c >= lim ? v0 : INT_MAX;
                         v1 = c + 1 >= lim ? v1 : INT_MAX;
@@ -237,27 +254,9 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) 
                         v3 = c + 3 >= lim ? v3 : INT_MAX;
                     }
                     const int mv = min(min(v0, v1), min(v2, v3));
-                    if (mv < m) {  // rare: a new first minimum in this lane's columns
-                        if (v0 == mv) {
-                            cm = c;
-                            e0 = a0;
-                            e1 = b0;
-                        } else if (v1 == mv) {
-                            cm = c + 1;
-                            e0 = a1;
-                            e1 = b1;
-                        } else if (v2 == mv) {
-                            cm = c + 2;
-                            e0 = a2;
-                            e1 = b2;
-                        } else {
-                            cm = c + 3;
-                            e0 = a3;
-                            e1 = b3;
-                        }
-                        m = mv;
-                    }
-                    q = rb.z;
+                    cm = mv < m ? c : cm;  // first group holding the lane minimum
+                    m = min(m, mv);
+                    q = rb4.z;
                     c += 4;
                 };
                 // groups starting below I+33 hold the diagonal triangle
@@ -265,10 +264,26 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) 
                 while (c < cmask) group(true);
                 while (c < cend) group(false);
                 if (m != INT_MAX && lim != INT_MAX) {  // idle lanes own no row
-                    const unsigned long long k =
-                        pack_key(m + smi2[rec2 + I + lane].y, I + lane, cm);
-                    if (k < key) {
-                        key = k;
+                    // Against the lane's earlier tiles (other rows) the group
+                    // start orders this candidate exactly; only when it wins is
+                    // its column found in the group, with the two costs there.
+                    const int dl = m + smi2[rec2 + I + lane].y;
+                    if (pack_key(dl, I + lane, cm) < key) {
+                        int qv = smi2[rec2 + cm - 1].x;
+                        int jx = -1, e0 = 0, e1 = 0;
+#pragma unroll
+                        for (int u = 0; u < 4; ++u) {
+                            const int2 r = smi2[rec2 + cm + u];
+                            const int a_ = smi[p1 + qv], b_ = smi[p2 + r.x];
+                            const int v = cm + u >= lim ? a_ + b_ + r.y : INT_MAX;
+                            if (jx < 0 && v == m) {
+                                jx = cm + u;
+                                e0 = a_;
+                                e1 = b_;
+                            }
+                            qv = r.x;
+                        }
+                        key = pack_key(dl, I + lane, jx);
                         ke0 = e0;
                         ke1 = e1;
                     }
@@ -276,47 +291,47 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) 
             }
             ++passes;
             const unsigned long long kw = warp_min_u64(key);
-            if (lane == 0) s_key[warp] = kw;
-            __syncthreads();
+            if (lane == 0) s_keyg[warp] = kw;
+            group_sync<TPC>(grp);
             if (warp == 0) {
-                unsigned long long kk = lane < kWarps ? s_key[lane] : ~0ull;
+                unsigned long long kk = lane < WPT ? s_keyg[lane] : ~0ull;
                 kk = warp_min_u64(kk);
-                if (lane == 0) s_best = kk;
+                if (lane == 0) s_best[grp] = kk;
             }
-            __syncthreads();
-            const unsigned long long best = s_best;
+            group_sync<TPC>(grp);
+            const unsigned long long best = s_best[grp];
             if (best == ~0ull) break;
             const int bd = static_cast<int>(static_cast<uint32_t>(best >> 32) ^ 0x80000000u);
             if (bd >= 0) break;
             if (key == best) {  // exactly one lane evaluated (i*, j*)
-                s_e0 = ke0;
-                s_e1 = ke1;
+                s_e0[grp] = ke0;
+                s_e1[grp] = ke1;
             }
-            __syncthreads();
+            group_sync<TPC>(grp);
             const int bi = static_cast<int>((best >> 16) & 0xffffu);
             const int bj = static_cast<int>(best & 0xffffu);
-            const int ei = s_e0, ej = s_e1;
+            const int ei = s_e0[grp], ej = s_e1[grp];
             // reverse x[bi+1..bj] and the edge terms strictly between bi and bj
-            for (int q2 = tid; q2 < (bj - bi) / 2; q2 += kThreads) {
+            for (int q2 = tid; q2 < (bj - bi) / 2; q2 += GT) {
                 const uint16_t t0 = smu[xs16 + bi + 1 + q2];
                 smu[xs16 + bi + 1 + q2] = smu[xs16 + bj - q2];
                 smu[xs16 + bj - q2] = t0;
             }
-            for (int q2 = tid; q2 < (bj - bi - 1) / 2; q2 += kThreads) {
+            for (int q2 = tid; q2 < (bj - bi - 1) / 2; q2 += GT) {
                 const int t0 = smi2[rec2 + bi + 1 + q2].y;
                 smi2[rec2 + bi + 1 + q2].y = smi2[rec2 + bj - 1 - q2].y;
                 smi2[rec2 + bj - 1 - q2].y = t0;
             }
-            __syncthreads();
-            for (int cc = bi + tid; cc <= bj; cc += kThreads)
+            group_sync<TPC>(grp);
+            for (int cc = bi + tid; cc <= bj; cc += GT)
                 smi2[rec2 + cc] = make_int2(smu[xs16 + cc + 1],
                                             cc == bi ? -ei : (cc == bj ? -ej : smi2[rec2 + cc].y));
             f += bd;
             ++moves;
-            __syncthreads();
+            group_sync<TPC>(grp);
         }
 
-        for (int i = tid; i < n; i += kThreads) tour[i] = smu[xs16 + i];
+        for (int i = tid; i < n; i += GT) tour[i] = smu[xs16 + i];
         if (tid == 0) {
             a.cost[p] = f;
             if (a.tour_passes) {
@@ -326,45 +341,69 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b) 
                 atomicAdd(a.pairs, static_cast<unsigned long long>(passes) * npairs);
                 atomicAdd(a.moves, static_cast<unsigned long long>(moves));
             }
-            s_pf = a.pbest ? a.pcost[p] : LLONG_MIN;
+            s_pf[grp] = a.pbest ? a.pcost[p] : LLONG_MIN;
         }
-        __syncthreads();
-        if (a.pbest && f < s_pf) {
+        group_sync<TPC>(grp);
+        if (a.pbest && f < s_pf[grp]) {
             uint16_t* pb = a.pbest + static_cast<size_t>(p) * a.ldt;
-            for (int i = tid; i < n; i += kThreads) pb[i] = smu[xs16 + i];
+            for (int i = tid; i < n; i += GT) pb[i] = smu[xs16 + i];
             if (tid == 0) a.pcost[p] = f;
         }
-        __syncthreads();
+        group_sync<TPC>(grp);
     }
 }
 
-template <int ROWS, int STAGES>
+// Shared bytes of one tour group, rounded to 128 bytes.
+size_t group_bytes(int n, int rows) { return (two_opt_tiled_smem(n, rows, 1) + 127) / 128 * 128; }
+
+template <int ROWS, int TPC>
 cudaError_t launch_cfg(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
-    const size_t smem = two_opt_tiled_smem(b.max_n, ROWS, STAGES);
-    cudaError_t e = cudaFuncSetAttribute(two_opt_tiled_kernel<ROWS, STAGES>,
+    const size_t gb = group_bytes(b.max_n, ROWS);
+    const size_t smem = gb * TPC;
+    cudaError_t e = cudaFuncSetAttribute(two_opt_tiled_kernel<ROWS, TPC>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two_opt_tiled_kernel<ROWS, STAGES>,
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two_opt_tiled_kernel<ROWS, TPC>,
                                                       kThreads, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
-    const int grid = max(1, min(b.total, per_sm * num_sms));
-    two_opt_tiled_kernel<ROWS, STAGES><<<grid, kThreads, smem, st>>>(b);
+    const int grid = max(1, min((b.total + TPC - 1) / TPC, per_sm * num_sms));
+    two_opt_tiled_kernel<ROWS, TPC>
+        <<<grid, kThreads, smem, st>>>(b, static_cast<int>(gb / sizeof(int)));
     return cudaGetLastError();
+}
+
+template <int ROWS>
+cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int num_sms, cudaStream_t st) {
+    switch (tpc) {
+        case 1: return launch_cfg<ROWS, 1>(b, num_sms, st);
+        case 2: return launch_cfg<ROWS, 2>(b, num_sms, st);
+        case 4: return launch_cfg<ROWS, 4>(b, num_sms, st);
+        default: return cudaErrorInvalidValue;
+    }
 }
 
 }  // namespace
 
 // Tile height for n (0 = no height fits): the tallest of 32 / 24 / 16 / 8 rows
-// whose single-stage tile fits in 220 KB of shared memory.  One stage is used:
-// at the sizes measured, more resident CTAs beat deeper pipelines.
+// whose tile fits in 220 KB of shared memory.  One buffer per tile: at the
+// sizes measured, more resident CTAs beat a deeper copy pipeline.
 int two_opt_tiled_rows(int n) {
     if (n < 3 || n > 65535) return 0;
     for (int rows : {32, 24, 16, 8})
         if (two_opt_tiled_smem(n, rows, 1) <= 220 * 1024) return rows;
     return 0;
+}
+
+// Tours per CTA for n at this tile height: short tours share a CTA so that
+// each warp keeps a long column range per tile (4 below 128 viewpoints, 2
+// below 256), as far as the groups' shared slices fit in 220 KB.
+int two_opt_tiled_tpc(int n, int rows) {
+    int tpc = n <= 128 ? 4 : (n <= 256 ? 2 : 1);
+    while (tpc > 1 && group_bytes(n, rows) * tpc > 220 * 1024) tpc /= 2;
+    return tpc;
 }
 
 cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStream_t st) {
@@ -373,14 +412,19 @@ cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStre
     return cudaGetLastError();
 }
 
-cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int num_sms, cudaStream_t st) {
-    if (!b.shifted || two_opt_tiled_smem(b.max_n, rows, 1) > 220 * 1024)
-        return cudaErrorInvalidValue;
+bool two_opt_tiled_fits(int n, int rows, int tpc) {
+    return n >= 3 && n <= 65535 && (rows == 32 || rows == 24 || rows == 16 || rows == 8) &&
+           (tpc == 1 || tpc == 2 || tpc == 4) && group_bytes(n, rows) * tpc <= 220 * 1024;
+}
+
+cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int tpc, int num_sms,
+                                 cudaStream_t st) {
+    if (!b.shifted || !two_opt_tiled_fits(b.max_n, rows, tpc)) return cudaErrorInvalidValue;
     switch (rows) {
-        case 32: return launch_cfg<32, 1>(b, num_sms, st);
-        case 24: return launch_cfg<24, 1>(b, num_sms, st);
-        case 16: return launch_cfg<16, 1>(b, num_sms, st);
-        case 8: return launch_cfg<8, 1>(b, num_sms, st);
+        case 32: return launch_rows<32>(b, tpc, num_sms, st);
+        case 24: return launch_rows<24>(b, tpc, num_sms, st);
+        case 16: return launch_rows<16>(b, tpc, num_sms, st);
+        case 8: return launch_rows<8>(b, tpc, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }

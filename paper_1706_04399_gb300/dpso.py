@@ -133,7 +133,8 @@ def lib():
             "dpso_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32,
                                                  _vp]),
             "dpso_batch_step": (ctypes.c_int, [_vp, _i32, _vp]),
-            "dpso_batch_autotune": (ctypes.c_int, [_vp, _i32p, _vp]),
+            "dpso_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _vp]),
+            "dpso_batch_set_two_opt_shape": (ctypes.c_int, [_vp, _i32, _i32]),
             "dpso_batch_destroy": (None, [_vp]),
             "dpso_probe_l2_read_gbs": (ctypes.c_int, [ctypes.c_size_t, _i32,
                                                       ctypes.POINTER(ctypes.c_double), _vp]),
@@ -372,11 +373,17 @@ class Batch:
     def step(self, iterations: int, stream=None):
         _check(lib().dpso_batch_step(self._h, iterations, _stream(stream)), "dpso_batch_step")
 
-    def autotune(self, stream=None) -> int:
+    def autotune(self, stream=None) -> tuple[int, int]:
+        """Chosen 2-opt launch shape: (tile height, tours per CTA)."""
         rows = ctypes.c_int32(0)
-        _check(lib().dpso_batch_autotune(self._h, ctypes.byref(rows), _stream(stream)),
-               "dpso_batch_autotune")
-        return rows.value
+        tpc = ctypes.c_int32(0)
+        _check(lib().dpso_batch_autotune(self._h, ctypes.byref(rows), ctypes.byref(tpc),
+                                         _stream(stream)), "dpso_batch_autotune")
+        return rows.value, tpc.value
+
+    def set_two_opt_shape(self, rows: int, tpc: int):
+        _check(lib().dpso_batch_set_two_opt_shape(self._h, rows, tpc),
+               "dpso_batch_set_two_opt_shape")
 
     def close(self):
         if getattr(self, "_h", None) and self._h.value:

@@ -82,8 +82,8 @@ def test_batch_autotune_keeps_results_and_matches_oracle():
     Cs = [cost_matrix_gpu(inst) for inst, _, _ in members]
     swarms = [dpso.Swarm(C, inst.n, inst.tags, p, seed) for C, (inst, p, seed) in zip(Cs, members)]
     batch = dpso.Batch(swarms)
-    rows = batch.autotune()
-    assert rows in (32, 24, 16, 8)
+    rows, tpc = batch.autotune()
+    assert rows in (32, 24, 16, 8) and tpc in (1, 2, 4)
     batch.step(5)
     for C, sw, (inst, p, seed) in zip(Cs, swarms, members):
         C_np, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
@@ -123,3 +123,29 @@ def test_batch_rejects_bad_members():
         dpso.Batch([sw, sw])
     with pytest.raises(dpso.DpsoError):
         dpso.Batch([])
+
+
+@pytest.mark.parametrize("rows", [32, 24, 16, 8])
+def test_every_two_opt_shape_gives_identical_states(rows):
+    """Each (tile height, tours per CTA) launch shape that fits gives the same
+    trajectories: members of uneven size under one shape match solo runs."""
+    specs = [(23, 0, 40), (70, 2, 24), (121, 3, 33), (190, 1, 17)]
+    members = []
+    for k, (n, m, S) in enumerate(specs):
+        inst = inputs.random_instance(n, m, 880 + k)
+        members.append((inst, dpso.default_params(swarm=S), 60 + k))
+    Cs = [cost_matrix_gpu(inst) for inst, _, _ in members]
+    want = [_solo_state(C, inst, p, seed, 6)[0] for C, (inst, p, seed) in zip(Cs, members)]
+    for tpc in (1, 2, 4):
+        swarms = [dpso.Swarm(C, inst.n, inst.tags, p, seed)
+                  for C, (inst, p, seed) in zip(Cs, members)]
+        batch = dpso.Batch(swarms)
+        batch.set_two_opt_shape(rows, tpc)
+        batch.step(6)
+        for sw, w, (inst, _, _) in zip(swarms, want, members):
+            got = sw.state()
+            for key in KEYS:
+                assert np.array_equal(got[key], w[key]), (rows, tpc, inst.n, key)
+        batch.close()
+        for sw in swarms:
+            sw.close()

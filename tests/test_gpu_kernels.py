@@ -149,6 +149,19 @@ def test_two_opt_large_tiles_capped_bitwise(n, moves):
     _two_opt_case(C_np, inputs.random_tours(n, 3, n), max_moves=moves)
 
 
+@pytest.mark.parametrize("n", [37, 101, 403])
+def test_two_opt_extreme_costs_bitwise(n):
+    # entries at the top of the allowed range: the padding columns past n must
+    # neither wrap nor look improving
+    rng = np.random.default_rng(n)
+    top = rng.integers(dpso.COST_MAX - 3, dpso.COST_MAX + 1, size=(n, n))
+    top = np.triu(top, 1)
+    C_np = np.ascontiguousarray((top + top.T).astype(np.int32))
+    _two_opt_case(C_np, inputs.random_tours(n, 5, n + 7))
+    _two_opt_case(inputs.random_cost_matrix(n, n + 9, hi=dpso.COST_MAX),
+                  inputs.random_tours(n, 5, n + 8))
+
+
 def test_two_opt_already_optimal_and_max_moves():
     n = 50
     C_np = inputs.random_cost_matrix(n, 11)

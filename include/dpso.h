@@ -256,14 +256,14 @@ void dpso_destroy(dpso_swarm *s);
 typedef struct dpso_batch dpso_batch;
 int dpso_batch_create(dpso_batch **out, dpso_swarm *const *swarms, int32_t count, void *stream);
 int dpso_batch_step(dpso_batch *b, int32_t iterations, void *stream);
-/* Picks the 2-opt launch shape for this batch, the tile height (32 / 24 / 16
- * / 8 rows) and the tours per CTA (1 / 2 / 4), by timing every shape that
+/* Picks the 2-opt launch shape for this batch, the tile height (32 / 30 /
+ * 24 / 16 / 8 rows) and the tours per CTA (1 / 2 / 4), by timing every shape that
  * fits on scratch copies of the members' current tours (at most 8 moves per
  * tour each, so the probe costs a few passes; best called right after
  * creation).  Results do not depend on the choice.  *rows_out and *tpc_out
  * (either may be NULL) receive the shape in use.  Synchronises `stream`. */
 int dpso_batch_autotune(dpso_batch *b, int32_t *rows_out, int32_t *tpc_out, void *stream);
-/* Sets the 2-opt launch shape by hand (rows 32 / 24 / 16 / 8, tours per CTA
+/* Sets the 2-opt launch shape by hand (rows 32 / 30 / 24 / 16 / 8, tours per CTA
  * 1 / 2 / 4; both 0: the defaults for the longest member).  DPSO_ERR_ARG when
  * the shape does not fit in shared memory for the longest member, or the
  * batch's members lack the row-shifted cost copies the tiled kernel reads.

@@ -965,7 +965,7 @@ int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, int32_t* tpc_out, void
             CK(cudaEventCreate(&e0));
             CK(cudaEventCreate(&e1));
             float best = 1e30f;
-            for (int rows : {32, 24, 16, 8}) {
+            for (int rows : {32, 30, 24, 16, 8}) {
                 for (int tpc : {1, 2, 4}) {
                     for (size_t i = 0; i < tasks.size(); ++i) {  // restore the tours
                         CK(cudaMemcpy2DAsync(tasks[i].tours, sizeof(uint16_t) * tasks[i].ldt,

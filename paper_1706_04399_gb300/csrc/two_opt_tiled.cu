@@ -16,9 +16,9 @@
 //    four copies whose rows are shifted right by 0..3 words; row a of a tile is
 //    taken from copy (a>>3)&3 into a row pitch ldq with ldq/4 odd, so the 32
 //    lanes reading one column hit 32 distinct banks.
-//  * Column records rec[c] = {x_c+1, -C[x_c][x_c+1]} give the second gather's
-//    column and the edge term in one broadcast load; the first gather's column
-//    x_c is the previous record's.
+//  * Column records rec[c] = {4 x_c+1, -C[x_c][x_c+1]} give the second
+//    gather's byte offset and the edge term in one broadcast load; the first
+//    gather's offset 4 x_c is the previous record's.
 //  * Each lane tracks, over its columns in increasing order (groups of four),
 //    the minimum of C[x_i][x_c] + C[x_i+1][x_c+1] - C[x_c][x_c+1] and the
 //    first group holding it, with selects only (no divergent branch in the
@@ -131,7 +131,8 @@ __device__ __forceinline__ void group_sync(int grp) {
 // tour in its own slice of shared memory (`group_words` ints, 128-byte
 // aligned), so short tours still give every warp a long column range.
 template <int ROWS, int TPC>
-__global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
+__global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
+    two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
     constexpr int kRows = ROWS;        // positions per tile, one per lane
     constexpr int kStaged = ROWS + 1;  // cost rows staged per tile
     constexpr int WPT = kWarps / TPC;  // warps per tour
@@ -175,26 +176,31 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, 
         const int rec2 = buf_words / 2;         // int2 index of record 0 (even)
         const int xs16 = (rec2 + n + 4) * 4;    // uint16 index of x_0
         const int* __restrict__ C = a.C;
-        const int* __restrict__ Cs = a.Cs;
         const int ldc = a.ldc;
         const long long npairs = static_cast<long long>(n) * (n - 3) / 2;
         const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
         const int guard = 1000 + 100 * n;
 
-        // The group's threads copy the cost rows of the tile starting at I.
+        // The group's threads copy the cost rows of the tile starting at I:
+        // lane l moves 16-byte chunks l, l+32, ... of each row.  Offsets into
+        // the shifted copies fit 32 bits (4 n ldq words < 2^30 for n <= 8192).
+        const char* __restrict__ csb = reinterpret_cast<const char*>(a.Cs) + lane * 16;
+        char* const tileb = reinterpret_cast<char*>(smi) + lane * 16;
+        const bool ch0 = lane < q16, ch1 = 32 + lane < q16, ch2 = 64 + lane < q16,
+                   ch3 = 96 + lane < q16;
+        const unsigned row_bytes = static_cast<unsigned>(ldq) * 4u;
         auto stage = [&](int I) {
             const int count = min(kStaged, n - 1 - I);
             for (int r = warp; r < count; r += WPT) {
-                const int k = (r >> 3) & 3;
-                const char* src =
-                    reinterpret_cast<const char*>(
-                        Cs + (static_cast<size_t>(k) * n + smu[xs16 + I + r]) * ldq) +
-                    lane * 16;
-                int* dst = smi + r * ldq + lane * 4;
-#pragma unroll
-                for (int j = 0; j < 4; ++j)
-                    if (j * 32 + lane < q16) cp_async16(dst + j * 128, src + j * 512);
-                for (int j = 4; j * 32 + lane < q16; ++j) cp_async16(dst + j * 128, src + j * 512);
+                const unsigned k = (r >> 3) & 3;
+                const unsigned off = (k * static_cast<unsigned>(n) + smu[xs16 + I + r]) * row_bytes;
+                const char* src = csb + off;
+                char* dst = tileb + r * row_bytes;
+                if (ch0) cp_async16(dst, src);
+                if (ch1) cp_async16(dst + 512, src + 512);
+                if (ch2) cp_async16(dst + 1024, src + 1024);
+                if (ch3) cp_async16(dst + 1536, src + 1536);
+                for (int j = 4; j * 32 + lane < q16; ++j) cp_async16(dst + j * 512, src + j * 512);
             }
         };
 
@@ -204,7 +210,7 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, 
         group_sync<TPC>(grp);
         for (int c = tid; c < n; c += GT) {
             const int u = smu[xs16 + c], v = smu[xs16 + c + 1];
-            smi2[rec2 + c] = make_int2(v, -C[static_cast<size_t>(u) * ldc + v]);
+            smi2[rec2 + c] = make_int2(4 * v, -C[static_cast<size_t>(u) * ldc + v]);
         }
         if (tid < 4) smi2[rec2 + n + tid] = make_int2(0, kPadCost);
         long long f = a.cost[p];
@@ -226,10 +232,13 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, 
                 cp_async_commit();
                 cp_async_wait<0>();
                 group_sync<TPC>(grp);
-                // lanes past the tile height idle on a valid row
+                // lanes past the tile height idle on a valid row; byte offsets
+                // of this lane's two rows (row start plus its 0..3 word shift)
                 const int ra = min(lane, kRows - 1), rb1 = min(lane + 1, kRows);
                 const int p1 = ra * ldq + ((ra >> 3) & 3);
                 const int p2 = rb1 * ldq + ((rb1 >> 3) & 3);
+                const char* const r1 = reinterpret_cast<const char*>(smi + p1);
+                const char* const r2 = reinterpret_cast<const char*>(smi + p2);
                 // columns in groups of four, contiguous per warp; the records
                 // past n are padding
                 const int cbeg = I + 2;
@@ -240,13 +249,17 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, 
                 int m = INT_MAX, cm = 0;
                 int c = cbeg + 4 * g0;
                 const int cend = cbeg + 4 * g1;
-                int q = g0 < g1 ? smi2[rec2 + c - 1].x : 0;  // x_c
+                int q = g0 < g1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
+                const int4* rp = smi4 + ((rec2 + c) >> 1);   // records c .. c+3
+                auto at = [](const char* row, int off) {
+                    return *reinterpret_cast<const int*>(row + off);
+                };
                 auto group = [&](bool masked) {
-                    const int4 ra4 = smi4[(rec2 + c) >> 1], rb4 = smi4[(rec2 + c + 2) >> 1];
-                    int v0 = smi[p1 + q] + smi[p2 + ra4.x] + ra4.y;
-                    int v1 = smi[p1 + ra4.x] + smi[p2 + ra4.z] + ra4.w;
-                    int v2 = smi[p1 + ra4.z] + smi[p2 + rb4.x] + rb4.y;
-                    int v3 = smi[p1 + rb4.x] + smi[p2 + rb4.z] + rb4.w;
+                    const int4 ra4 = rp[0], rb4 = rp[1];
+                    int v0 = at(r1, q) + at(r2, ra4.x) + ra4.y;
+                    int v1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w;
+                    int v2 = at(r1, ra4.z) + at(r2, rb4.x) + rb4.y;
+                    int v3 = at(r1, rb4.x) + at(r2, rb4.z) + rb4.w;
                     if (masked) {
                         v0 = c >= lim ? v0 : INT_MAX;
                         v1 = c + 1 >= lim ? v1 : INT_MAX;
@@ -258,6 +271,7 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, 
                     m = min(m, mv);
                     q = rb4.z;
                     c += 4;
+                    rp += 2;
                 };
                 // groups starting below I+33 hold the diagonal triangle
                 const int cmask = min(cend, I + kStaged);
@@ -274,7 +288,7 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, 
 #pragma unroll
                         for (int u = 0; u < 4; ++u) {
                             const int2 r = smi2[rec2 + cm + u];
-                            const int a_ = smi[p1 + qv], b_ = smi[p2 + r.x];
+                            const int a_ = at(r1, qv), b_ = at(r2, r.x);
                             const int v = cm + u >= lim ? a_ + b_ + r.y : INT_MAX;
                             if (jx < 0 && v == m) {
                                 jx = cm + u;
@@ -324,7 +338,7 @@ __global__ void __launch_bounds__(kThreads) two_opt_tiled_kernel(TwoOptBatch b, 
             }
             group_sync<TPC>(grp);
             for (int cc = bi + tid; cc <= bj; cc += GT)
-                smi2[rec2 + cc] = make_int2(smu[xs16 + cc + 1],
+                smi2[rec2 + cc] = make_int2(4 * smu[xs16 + cc + 1],
                                             cc == bi ? -ei : (cc == bj ? -ej : smi2[rec2 + cc].y));
             f += bd;
             ++moves;
@@ -387,19 +401,23 @@ cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int num_sms, cudaStream_t
 
 }  // namespace
 
-// Tile height for n (0 = no height fits): the tallest of 32 / 24 / 16 / 8 rows
-// whose tile fits in 220 KB of shared memory.  One buffer per tile: at the
-// sizes measured, more resident CTAs beat a deeper copy pipeline.
+// Default launch shape for tours of n viewpoints, from a sweep on GB300 of
+// full 2-opt runs on random tours (n = 50 .. 600): 32-row tiles with 4 tours
+// per CTA up to n = 128; 30-row tiles (4 CTAs per SM, the kernel being held
+// to 64 registers) with 2 tours per CTA up to n = 256 and 1 while four such
+// CTAs fit in an SM's 228 KB; beyond that the tallest of 32 / 24 / 16 / 8
+// rows whose tile fits in 220 KB, 1 tour per CTA.  One buffer per tile: at
+// the sizes measured, more resident CTAs beat a deeper copy pipeline.
+// two_opt_tiled_rows returns 0 when no tile height fits.
 int two_opt_tiled_rows(int n) {
     if (n < 3 || n > 65535) return 0;
+    if (n <= 128) return 32;
+    if (4 * (group_bytes(n, 30) * (n <= 256 ? 2 : 1) + 1024) <= 228 * 1024) return 30;
     for (int rows : {32, 24, 16, 8})
         if (two_opt_tiled_smem(n, rows, 1) <= 220 * 1024) return rows;
     return 0;
 }
 
-// Tours per CTA for n at this tile height: short tours share a CTA so that
-// each warp keeps a long column range per tile (4 below 128 viewpoints, 2
-// below 256), as far as the groups' shared slices fit in 220 KB.
 int two_opt_tiled_tpc(int n, int rows) {
     int tpc = n <= 128 ? 4 : (n <= 256 ? 2 : 1);
     while (tpc > 1 && group_bytes(n, rows) * tpc > 220 * 1024) tpc /= 2;
@@ -413,7 +431,8 @@ cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStre
 }
 
 bool two_opt_tiled_fits(int n, int rows, int tpc) {
-    return n >= 3 && n <= 65535 && (rows == 32 || rows == 24 || rows == 16 || rows == 8) &&
+    return n >= 3 && n <= 65535 &&
+           (rows == 32 || rows == 30 || rows == 24 || rows == 16 || rows == 8) &&
            (tpc == 1 || tpc == 2 || tpc == 4) && group_bytes(n, rows) * tpc <= 220 * 1024;
 }
 
@@ -422,6 +441,7 @@ cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int tpc, int nu
     if (!b.shifted || !two_opt_tiled_fits(b.max_n, rows, tpc)) return cudaErrorInvalidValue;
     switch (rows) {
         case 32: return launch_rows<32>(b, tpc, num_sms, st);
+        case 30: return launch_rows<30>(b, tpc, num_sms, st);
         case 24: return launch_rows<24>(b, tpc, num_sms, st);
         case 16: return launch_rows<16>(b, tpc, num_sms, st);
         case 8: return launch_rows<8>(b, tpc, num_sms, st);

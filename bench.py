@@ -220,6 +220,21 @@ def two_opt_traffic(workload_name: str):
     return rec.get("dram_bytes_per_launch")
 
 
+def max_over_ranks(value: float, dist=None, device="cpu") -> float:
+    """The largest `value` over all ranks (the job's time is its slowest rank)."""
+    if dist is None:
+        return value
+    import torch
+    t = torch.tensor([value], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_throughput(units_per_rank: int, world: int, max_ms: float) -> float:
+    """Whole-job rate: the units every rank processed over the slowest rank's time."""
+    return units_per_rank * world / (max_ms / 1e3)
+
+
 def gpu_line(args):
     import numpy as np
     import torch
@@ -273,14 +288,8 @@ def gpu_line(args):
     dev_ms = sum(a.elapsed_time(b) for a, b in evs)
     timing = sw.timing()
     st1 = sw.stats()
-    if dist:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms_max = float(t.item())
-    else:
-        dev_ms_max = dev_ms
-    units = world * S * args.steps
-    value = units / (dev_ms_max / 1e3)
+    dev_ms_max = max_over_ranks(dev_ms, dist, "cuda")
+    value = job_throughput(S * args.steps, world, dev_ms_max)
 
     pairs = st1["two_opt_pairs"] - st0["two_opt_pairs"]
     moves = st1["two_opt_moves"] - st0["two_opt_moves"]

@@ -1,0 +1,70 @@
+"""bench.py's multi-rank bookkeeping on CPU: two gloo ranks (spawned) agree on
+the slowest rank's time and the whole-job rate, and the reference arm does
+its work on rank 0 only."""
+import io
+import os
+import sys
+import contextlib
+
+import pytest
+
+from conftest import ROOT
+
+torch = pytest.importorskip("torch")
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def _rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    ms = 100.0 + 50.0 * rank            # rank 1 is the slow one
+    mx = bench.max_over_ranks(ms, dist, "cpu")
+    units = 1024 * 30                   # particles x timed generations per rank
+    out.put((rank, mx, bench.job_throughput(units, world, mx)))
+    dist.barrier()
+    dist.destroy_process_group()
+
+
+def test_two_gloo_ranks_agree_on_max_time_and_job_rate():
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = 29500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_rank, args=(r, 2, port, q)) for r in range(2)]
+    for p in procs:
+        p.start()
+    got = sorted(q.get(timeout=120) for _ in procs)
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    assert [g[1] for g in got] == [150.0, 150.0]
+    # both ranks' units over the slowest rank's time
+    assert got[0][2] == got[1][2] == pytest.approx(2 * 1024 * 30 / 0.150)
+
+
+def test_single_rank_needs_no_process_group():
+    assert bench.max_over_ranks(12.5) == 12.5
+    assert bench.job_throughput(100, 1, 1000.0) == pytest.approx(100.0)
+
+
+def test_reference_arm_runs_on_rank_zero_only(monkeypatch):
+    monkeypatch.setenv("RANK", "1")
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        rc = bench.main(["--impl", "reference", "--steps", "1", "--warmup", "0",
+                         "--workload", "tiny"])
+    assert rc == 0 and buf.getvalue() == ""
+
+
+def test_reference_arm_line(monkeypatch):
+    import json
+    monkeypatch.setenv("RANK", "0")
+    buf = io.StringIO()
+    with contextlib.redirect_stdout(buf):
+        rc = bench.main(["--impl", "reference", "--steps", "2", "--warmup", "0",
+                         "--workload", "tiny"])
+    line = json.loads(buf.getvalue())
+    assert rc == 0 and line["impl"] == "reference" and line["value"] > 0
+    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["e2e"]["h2d_bytes_per_step"] == 0

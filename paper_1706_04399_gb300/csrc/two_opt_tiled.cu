@@ -7,10 +7,11 @@
 //
 // Layout and mapping:
 //  * One CTA per tour (persistent grid, work queue), 8 warps.
-//  * A tile is 32 positions I..I+31, one per lane; its 33 cost rows
-//    C[x_I..x_I+32] are staged in shared memory with 16-byte cp.async copies
-//    issued by all threads, in a STAGES-deep pipeline (commit / wait groups),
-//    so the next tiles load while the current one is evaluated.
+//  * A tile is R positions I..I+R-1 (R = 32 or 30; fewer for long tours), one
+//    per lane; its R+1 cost rows C[x_I..x_I+R] are staged in shared memory,
+//    one bulk copy per row posted by one lane of the group's first warp and
+//    counted on an mbarrier (a tile costs a handful of instructions instead
+//    of one 16-byte copy per lane-chunk).
 //  * 16-byte copies need 16-byte-aligned rows, which alone would put rows a,
 //    a+8, a+16, a+24 in the same bank.  The cost matrix is therefore kept in
 //    four copies whose rows are shifted right by 0..3 words; row a of a tile is
@@ -40,18 +41,18 @@ namespace {
 constexpr int kWarps = 8;
 constexpr int kThreads = kWarps * 32;
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    const unsigned s = static_cast<unsigned>(__cvta_generic_to_shared(smem));
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ unsigned smem_addr(const void* p) {
+    return static_cast<unsigned>(__cvta_generic_to_shared(p));
 }
 
-__device__ __forceinline__ void cp_async_commit() {
-    asm volatile("cp.async.commit_group;\n" ::: "memory");
-}
-
-template <int N>
-__device__ __forceinline__ void cp_async_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+// One row of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
+// global to this CTA's shared memory by the bulk-copy engine; completion is
+// counted in bytes on the mbarrier at `mbar`.
+__device__ __forceinline__ void bulk_row(unsigned dst, const void* src, unsigned bytes,
+                                         unsigned mbar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
+        ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
 }
 
 // (delta, i, j) -> order-preserving 64-bit key: biased delta, then i, then j.
@@ -146,6 +147,8 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
     __shared__ unsigned long long s_best[TPC];
     __shared__ int s_part[TPC], s_e0[TPC], s_e1[TPC];
     __shared__ long long s_pf[TPC];
+    __shared__ __align__(8) unsigned long long s_mbar[TPC];  // tile-arrival barrier per group
+    __shared__ int s_abort[TPC];  // a tile copy did not complete: the group stops
 
     const int lane = threadIdx.x & 31;
     const int grp = (threadIdx.x >> 5) / WPT;  // tour group
@@ -157,6 +160,13 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
     uint16_t* smu = reinterpret_cast<uint16_t*>(smi);
     unsigned long long* s_keyg = s_key + grp * WPT;
 
+    const unsigned mbar = smem_addr(&s_mbar[grp]);
+    unsigned phase = 0;  // parity of the tile-arrival phase to wait for
+    if (tid == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+        s_abort[grp] = 0;
+    }
     for (;;) {
         if (tid == 0) s_part[grp] = static_cast<int>(atomicAdd(b.queue, 1u));
         group_sync<TPC>(grp);
@@ -171,7 +181,6 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
         }
         const int n = a.n;
         const int ldq = shifted_ld(n);
-        const int q16 = ldq / 4;
         const int buf_words = kStaged * ldq;
         const int rec2 = buf_words / 2;         // int2 index of record 0 (even)
         const int xs16 = (rec2 + n + 4) * 4;    // uint16 index of x_0
@@ -181,27 +190,49 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
         const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
         const int guard = 1000 + 100 * n;
 
-        // The group's threads copy the cost rows of the tile starting at I:
-        // lane l moves 16-byte chunks l, l+32, ... of each row.  Offsets into
-        // the shifted copies fit 32 bits (4 n ldq words < 2^30 for n <= 8192).
-        const char* __restrict__ csb = reinterpret_cast<const char*>(a.Cs) + lane * 16;
-        char* const tileb = reinterpret_cast<char*>(smi) + lane * 16;
-        const bool ch0 = lane < q16, ch1 = 32 + lane < q16, ch2 = 64 + lane < q16,
-                   ch3 = 96 + lane < q16;
+        // Warp 0 of the group stages the cost rows of the tile starting at I:
+        // lane r posts row r as one bulk copy (row r from shifted copy
+        // (r>>3)&3); lane 0 first arms the barrier with the tile's bytes.
+        // Offsets into the shifted copies fit 32 bits (4 n ldq words < 2^30).
+        const char* const cs0 = reinterpret_cast<const char*>(a.Cs);
+        const unsigned tile_s = smem_addr(smi);
         const unsigned row_bytes = static_cast<unsigned>(ldq) * 4u;
         auto stage = [&](int I) {
             const int count = min(kStaged, n - 1 - I);
-            for (int r = warp; r < count; r += WPT) {
-                const unsigned k = (r >> 3) & 3;
-                const unsigned off = (k * static_cast<unsigned>(n) + smu[xs16 + I + r]) * row_bytes;
-                const char* src = csb + off;
-                char* dst = tileb + r * row_bytes;
-                if (ch0) cp_async16(dst, src);
-                if (ch1) cp_async16(dst + 512, src + 512);
-                if (ch2) cp_async16(dst + 1024, src + 1024);
-                if (ch3) cp_async16(dst + 1536, src + 1536);
-                for (int j = 4; j * 32 + lane < q16; ++j) cp_async16(dst + j * 512, src + j * 512);
+            if (warp == 0) {
+                // the group barrier before this ordered the generic reads of
+                // the previous tile; this orders them before the async writes
+                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+                if (lane == 0)
+                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar),
+                                 "r"(static_cast<unsigned>(count) * row_bytes)
+                                 : "memory");
+                __syncwarp();
+                for (int r = lane; r < count; r += 32) {
+                    const unsigned k = (r >> 3) & 3;
+                    const unsigned off =
+                        (k * static_cast<unsigned>(n) + smu[xs16 + I + r]) * row_bytes;
+                    bulk_row(tile_s + r * row_bytes, cs0 + off, row_bytes, mbar);
+                }
             }
+        };
+        // Every thread waits for the tile's bytes, at most ~2 s of clock; a
+        // copy that never lands sets the group's abort flag and the status.
+        auto stage_wait = [&]() {
+            unsigned done = 0;
+            const long long t0 = clock64();
+            while (!done) {
+                asm volatile(
+                    "{ .reg .pred p; mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2; "
+                    "selp.u32 %0, 1, 0, p; }\n"
+                    : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
+                if (!done && clock64() - t0 > (1ll << 32)) {
+                    s_abort[grp] = 1;
+                    if (a.status) atomicExch(a.status, DPSO_ERR_TIMEOUT);
+                    break;
+                }
+            }
+            phase ^= 1u;
         };
 
         uint16_t* tour = a.tours + static_cast<size_t>(p) * a.ldt;
@@ -228,10 +259,9 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
             for (int t = 0; t < ntiles; ++t) {
                 const int I = t * kRows;
                 group_sync<TPC>(grp);  // the previous tile is no longer read
+                if (s_abort[grp]) break;  // read after the barrier: the group agrees
                 stage(I);
-                cp_async_commit();
-                cp_async_wait<0>();
-                group_sync<TPC>(grp);
+                stage_wait();
                 // lanes past the tile height idle on a valid row; byte offsets
                 // of this lane's two rows (row start plus its 0..3 word shift)
                 const int ra = min(lane, kRows - 1), rb1 = min(lane + 1, kRows);
@@ -307,6 +337,7 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
             const unsigned long long kw = warp_min_u64(key);
             if (lane == 0) s_keyg[warp] = kw;
             group_sync<TPC>(grp);
+            if (s_abort[grp]) break;  // no move from a pass with a missing tile
             if (warp == 0) {
                 unsigned long long kk = lane < WPT ? s_keyg[lane] : ~0ull;
                 kk = warp_min_u64(kk);
@@ -364,6 +395,7 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
             if (tid == 0) a.pcost[p] = f;
         }
         group_sync<TPC>(grp);
+        if (s_abort[grp]) break;  // copies are not completing: the group stops
     }
 }
 
@@ -401,20 +433,33 @@ cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int num_sms, cudaStream_t
 
 }  // namespace
 
-// Default launch shape for tours of n viewpoints, from a sweep on GB300 of
-// full 2-opt runs on random tours (n = 50 .. 600): 32-row tiles with 4 tours
-// per CTA up to n = 128; 30-row tiles (4 CTAs per SM, the kernel being held
-// to 64 registers) with 2 tours per CTA up to n = 256 and 1 while four such
-// CTAs fit in an SM's 228 KB; beyond that the tallest of 32 / 24 / 16 / 8
-// rows whose tile fits in 220 KB, 1 tour per CTA.  One buffer per tile: at
+// Resident CTAs per SM for a shape: shared memory (228 KB per SM, 1 KB
+// reserved per CTA) against registers (64 per thread at R = 30, else 80).
+static int tiled_ctas_per_sm(int n, int rows, int tpc) {
+    const int by_smem = static_cast<int>((228 * 1024) / (group_bytes(n, rows) * tpc + 1024));
+    return min(by_smem, rows == 30 ? 4 : 3);
+}
+
+// Default launch shape for tours of n viewpoints, from sweeps on GB300 of full
+// 2-opt runs on random tours (n = 50 .. 2000, enough tours to fill the GPU):
+// 32-row tiles with 4 tours per CTA up to n = 128; 30-row tiles (held to 64
+// registers so that four CTAs share an SM) with 2 tours per CTA up to 256 and
+// with 1 while four such CTAs fit; beyond that the tallest of 32 / 24 / 16 / 8
+// rows that fits in 220 KB, except that 24 rows win over a 32-row tile that
+// leaves a single CTA per SM when they allow two.  One buffer per tile: at
 // the sizes measured, more resident CTAs beat a deeper copy pipeline.
 // two_opt_tiled_rows returns 0 when no tile height fits.
 int two_opt_tiled_rows(int n) {
     if (n < 3 || n > 65535) return 0;
     if (n <= 128) return 32;
-    if (4 * (group_bytes(n, 30) * (n <= 256 ? 2 : 1) + 1024) <= 228 * 1024) return 30;
-    for (int rows : {32, 24, 16, 8})
-        if (two_opt_tiled_smem(n, rows, 1) <= 220 * 1024) return rows;
+    if (tiled_ctas_per_sm(n, 30, n <= 256 ? 2 : 1) >= 4) return 30;
+    for (int rows : {32, 24, 16, 8}) {
+        if (two_opt_tiled_smem(n, rows, 1) > 220 * 1024) continue;
+        if (rows == 32 && tiled_ctas_per_sm(n, 32, 1) == 1 &&
+            two_opt_tiled_smem(n, 24, 1) <= 220 * 1024 && tiled_ctas_per_sm(n, 24, 1) >= 2)
+            return 24;
+        return rows;
+    }
     return 0;
 }
 

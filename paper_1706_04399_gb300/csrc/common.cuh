@@ -101,6 +101,7 @@ struct SwarmDev {
     unsigned char* dup;        // mutation scratch: duplicate flags
     unsigned char* kept;       // mutation scratch: kept flags
     Ctl* ctl;
+    int* order;  // exchange order: particles by decreasing fitness (S ints)
 };
 
 inline int round_up(int v, int m) { return (v + m - 1) / m * m; }
@@ -129,6 +130,7 @@ struct BatchView {
     int total;    // off[ninst]: particles in the batch
     int max_ldn;  // largest ldn: sizes the move kernel's shared memory
     int arrays;   // shared arrays per particle in the move kernel: 7 if any w < 1, else 5
+    int max_S;    // largest swarm of the batch
 };
 
 // Instance owning global item g: the largest i with off[i] <= g.
@@ -157,6 +159,7 @@ cudaError_t launch_init_particles(const Consts& k, const SwarmDev& d, const uint
 cudaError_t launch_gbest_init(const Consts& k, const SwarmDev& d, cudaStream_t st);
 cudaError_t launch_move(const BatchView& b, cudaStream_t st);
 cudaError_t launch_mutation(const BatchView& b, cudaStream_t st);
+cudaError_t launch_rank_cost(const BatchView& b, cudaStream_t st);
 cudaError_t launch_gbest(const BatchView& b, int second, cudaStream_t st);
 cudaError_t launch_philox_draws(unsigned long long seed, uint32_t phase, uint32_t iter,
                                 uint32_t particle, int count, uint32_t* out, cudaStream_t st);
@@ -184,6 +187,10 @@ struct TwoOptTask {
     // and moves are written there instead of being added to *pairs / *moves.
     unsigned int* tour_passes;
     unsigned int* tour_moves;
+    // Optional processing order: work item k of this task is tour order[k]
+    // (a permutation of 0..count-1); NULL means tour k.  Results do not depend
+    // on it, only the time the last tour finishes does.
+    const int* order;
 };
 
 // One persistent launch over every tour of several problems: tasks[nprob] and

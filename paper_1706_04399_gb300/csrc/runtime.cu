@@ -86,6 +86,7 @@ struct dpso_swarm {
     long long *F = nullptr, *PF = nullptr;
     unsigned long long* hash = nullptr;
     unsigned char *dup = nullptr, *kept = nullptr;
+    int* order = nullptr;  // exchange order, recomputed every generation
     Ctl* ctl = nullptr;
     SwarmMeta* meta = nullptr;  // device: descriptors of this swarm as a batch of one
     long long* hist = nullptr;
@@ -109,8 +110,8 @@ void free_swarm(dpso_swarm* s) {
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
     if (s->g_plain) cudaGraphExecDestroy(s->g_plain);
     if (s->g_mut) cudaGraphExecDestroy(s->g_mut);
-    void* bufs[] = {s->C,   s->Cs,   s->X,   s->V,    s->P,   s->G,   s->F,
-                    s->PF,  s->hash, s->dup, s->kept, s->ctl, s->meta, s->hist};
+    void* bufs[] = {s->C,    s->Cs,   s->X,   s->V,     s->P,   s->G,    s->F,    s->PF,
+                    s->hash, s->dup,  s->kept, s->order, s->ctl, s->meta, s->hist};
     for (void* b : bufs)
         if (b) cudaFree(b);
     if (s->cap) cudaStreamDestroy(s->cap);
@@ -149,13 +150,14 @@ TwoOptTask swarm_task(const dpso_swarm* s) {
     a.pairs = &s->ctl->pairs;
     a.moves = &s->ctl->moves;
     a.status = &s->ctl->status;
+    a.order = s->order;
     return a;
 }
 
 int swarm_arrays(const Consts& k) { return k.w_q >= (1ull << 32) ? 5 : 7; }
 
 BatchView swarm_view(const dpso_swarm* s) {
-    return BatchView{&s->meta->desc, s->meta->off, 1, s->k.S, s->k.ldn, swarm_arrays(s->k)};
+    return BatchView{&s->meta->desc, s->meta->off, 1, s->k.S, s->k.ldn, swarm_arrays(s->k), s->k.S};
 }
 
 TwoOptBatch swarm_two_opt(const dpso_swarm* s) {
@@ -172,7 +174,8 @@ cudaError_t enqueue_batch_generation(const BatchView& bv, const TwoOptBatch& tb,
     if (e == cudaSuccess && with_mutation) e = launch_mutation(bv, st);
     if (e == cudaSuccess) e = launch_gbest(bv, 0, st);
     if (e == cudaSuccess && any_two_opt) {
-        e = cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st);
+        e = launch_rank_cost(bv, st);
+        if (e == cudaSuccess) e = cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st);
         if (e == cudaSuccess) e = launch_two_opt(tb, num_sms, st);
         if (e == cudaSuccess) e = launch_gbest(bv, 1, st);
     }
@@ -209,6 +212,7 @@ cudaError_t enqueue_generation_timed(dpso_swarm* s, bool mut_iter, cudaStream_t 
     if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
     if (e == cudaSuccess) e = launch_gbest(bv, 0, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
+    if (e == cudaSuccess && two) e = launch_rank_cost(bv, st);
     if (e == cudaSuccess && two) e = cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st);
     if (e == cudaSuccess && two) e = launch_two_opt(tb, s->num_sms, st);
     if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
@@ -502,11 +506,22 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
         (st = dalloc(&s->P, S * ldn, ust)) || (st = dalloc(&s->G, ldn, ust)) ||
         (st = dalloc(&s->F, S, ust)) || (st = dalloc(&s->PF, S, ust)) ||
         (st = dalloc(&s->hash, S, ust)) || (st = dalloc(&s->dup, S, ust)) ||
-        (st = dalloc(&s->kept, S, ust)) || (st = dalloc(&s->ctl, 1, ust)) ||
+        (st = dalloc(&s->kept, S, ust)) || (st = dalloc(&s->order, S, ust)) ||
+        (st = dalloc(&s->ctl, 1, ust)) ||
         (st = dalloc(&s->meta, 1, ust)))
         return fail(st);
     if ((st = ensure_history(s, 1024))) return fail(st);
-    s->d = SwarmDev{s->C, s->X, s->V, s->P, s->G, s->F, s->PF, s->hash, s->dup, s->kept, s->ctl};
+    s->d = SwarmDev{s->C,    s->X,   s->V,    s->P,   s->G,    s->F,
+                    s->PF,   s->hash, s->dup, s->kept, s->ctl, s->order};
+    {
+        // identity until the first generation ranks the particles
+        std::vector<int> ident(S);
+        for (size_t i = 0; i < S; ++i) ident[i] = static_cast<int>(i);
+        if (cudaMemcpyAsync(s->order, ident.data(), sizeof(int) * S, cudaMemcpyHostToDevice,
+                            ust) != cudaSuccess ||
+            cudaStreamSynchronize(ust) != cudaSuccess)
+            return fail(DPSO_ERR_CUDA);
+    }
 
     int* err = nullptr;
     uint16_t* orders = nullptr;
@@ -885,7 +900,9 @@ int dpso_batch_create(dpso_batch** out, dpso_swarm* const* swarms, int32_t count
             cudaSuccess ||
         cudaDeviceSynchronize() != cudaSuccess)
         return fail(DPSO_ERR_CUDA);
-    b->bv = BatchView{b->desc, b->off, count, off[count], max_ldn, arrays};
+    int max_S = 0;
+    for (int i = 0; i < count; ++i) max_S = std::max(max_S, swarms[i]->k.S);
+    b->bv = BatchView{b->desc, b->off, count, off[count], max_ldn, arrays, max_S};
     b->tb = TwoOptBatch{b->tasks, b->toff, nt, toff.back(), max_n, shifted, 0, b->queue};
     b->any_two_opt = nt > 0;
     if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
@@ -955,6 +972,7 @@ int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, int32_t* tpc_out, void
             t.moves = cnt + 1;
             t.status = status;
             t.max_moves = kProbeMoves;
+            t.order = nullptr;
         }
         TwoOptTask* dtasks = nullptr;
         if (!st2 && !(st2 = dalloc(&dtasks, tasks.size(), st))) {

@@ -70,7 +70,7 @@ size_t request_footprint(int n, int m, int S, int T, int flags) {
     if ((flags & DPSO_FLAG_TWO_OPT) && dpso::two_opt_tiled_rows(n) > 0)
         b += a(static_cast<size_t>(4) * n * dpso::shifted_ld(n) * 4);  // shifted copies
     b += 3 * a(s * ldn * 2) + a(ldn * 2);                             // X, V, P, G
-    b += 3 * a(s * 8) + 2 * a(s);                                     // F, PF, hash, dup, kept
+    b += 3 * a(s * 8) + 2 * a(s) + a(s * 4);                          // F, PF, hash, dup, kept, order
     b += a(hist * 8) + 2 * a(sizeof(SwarmDesc) + 1024);               // history, control, meta
     b += a(static_cast<size_t>(n) * 24) + a(static_cast<size_t>(std::max(m, 1)) * 48) +
          a(static_cast<size_t>(n) * n * 4) + a(ldn * 16) + a(static_cast<size_t>(n) * 12);

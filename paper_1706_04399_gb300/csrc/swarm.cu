@@ -496,6 +496,37 @@ __global__ void gbest_kernel(BatchView b, int second) {
     if (k.stall_limit > 0 && c->stall >= k.stall_limit) c->done = 1;
 }
 
+// ------------------------------------------------------ exchange order
+// order[r] = the particle of rank r by (fitness descending, index ascending)
+// within each instance, so the edge exchange starts the tours expected to
+// need the most passes first (longest-processing-time-first list
+// scheduling; the post-move fitness is the estimate).  Block (x, y) ranks
+// particles x*256 .. x*256+255 of instance y against all of its particles.
+__global__ void rank_cost_kernel(BatchView b) {
+    const int inst = blockIdx.y;
+    const SwarmDesc& ds = b.desc[inst];
+    const int S = ds.k.S;
+    const int p = blockIdx.x * blockDim.x + threadIdx.x;
+    if (blockIdx.x * blockDim.x >= S) return;  // whole block past this swarm
+    const long long* __restrict__ F = ds.d.F;
+    __shared__ long long sf[256];
+    const long long mine = p < S ? F[p] : 0;
+    int rank = 0;
+    for (int q0 = 0; q0 < S; q0 += 256) {
+        const int cnt = min(256, S - q0);
+        __syncthreads();
+        if (threadIdx.x < cnt) sf[threadIdx.x] = F[q0 + threadIdx.x];
+        __syncthreads();
+        if (p < S) {
+            for (int j = 0; j < cnt; ++j) {
+                const long long o = sf[j];
+                rank += (o > mine) | ((o == mine) & (q0 + j < p));
+            }
+        }
+    }
+    if (p < S) ds.d.order[rank] = p;
+}
+
 __global__ void philox_draws_kernel(unsigned long long seed, uint32_t phase, uint32_t iter,
                                     uint32_t particle, int count, uint32_t* out) {
     const int d = blockIdx.x * blockDim.x + threadIdx.x;
@@ -558,6 +589,13 @@ cudaError_t launch_mutation(const BatchView& b, cudaStream_t st) {
     mut_dup_kernel<<<tb, 256, 0, st>>>(b);
     mut_kept_kernel<<<tb, 256, 0, st>>>(b);
     mut_apply_kernel<<<wb, 256, 0, st>>>(b);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_rank_cost(const BatchView& b, cudaStream_t st) {
+    if (b.ninst <= 0 || b.max_S <= 0) return cudaSuccess;
+    dim3 grid((b.max_S + 255) / 256, b.ninst);
+    rank_cost_kernel<<<grid, 256, 0, st>>>(b);
     return cudaGetLastError();
 }
 

@@ -62,8 +62,8 @@ __global__ void __launch_bounds__(kWarps * 32) two_opt_kernel(TwoOptBatch b) {
         const int g = s_part;
         if (g >= b.total) break;
         const int prob = find_inst(b.off, b.nprob, g);
-        const int p = g - b.off[prob];
         const TwoOptTask a = b.tasks[prob];
+        const int p = a.order ? a.order[g - b.off[prob]] : g - b.off[prob];
         if (a.gate && *a.gate == 0) {  // this problem does not exchange edges now
             __syncthreads();
             continue;

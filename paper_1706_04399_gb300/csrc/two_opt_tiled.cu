@@ -173,8 +173,8 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
         const int g = s_part[grp];
         if (g >= b.total) break;
         const int prob = find_inst(b.off, b.nprob, g);
-        const int p = g - b.off[prob];
         const TwoOptTask a = b.tasks[prob];
+        const int p = a.order ? a.order[g - b.off[prob]] : g - b.off[prob];
         if (a.gate && *a.gate == 0) {  // this problem does not exchange edges now
             group_sync<TPC>(grp);
             continue;

@@ -401,7 +401,7 @@ def batched_line(args):
 
     together, alone = swarms(), swarms()
     batch = dpso.Batch(together, stream)
-    rows, tpc = batch.autotune(stream)
+    rows, tpc, tg = batch.autotune(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
     S_total = sum(i.swarm for i in insts)
 
@@ -448,6 +448,7 @@ def batched_line(args):
         "batched": {"one_per_launch_value": solo_value, "speedup": value / solo_value,
                     "one_per_launch_ms_per_step": ms_solo / args.steps,
                     "identical_states": identical, "two_opt_rows": rows, "two_opt_tours_per_cta": tpc,
+                    "two_opt_tiles_in_flight": tg,
                     "two_opt_pairs_per_s_over_step": pairs / (ms_batch / 1e3)},
         "gpu_launches": None, "roofline": None, "cpu_baseline": None, "e2e": None,
         "clocks": sampler.summary(),

@@ -256,19 +256,28 @@ void dpso_destroy(dpso_swarm *s);
 typedef struct dpso_batch dpso_batch;
 int dpso_batch_create(dpso_batch **out, dpso_swarm *const *swarms, int32_t count, void *stream);
 int dpso_batch_step(dpso_batch *b, int32_t iterations, void *stream);
-/* Picks the 2-opt launch shape for this batch, the tile height (32 / 30 /
- * 24 / 16 / 8 rows) and the tours per CTA (1 / 2 / 4), by timing every shape that
- * fits on scratch copies of the members' current tours (at most 8 moves per
- * tour each, so the probe costs a few passes; best called right after
- * creation).  Results do not depend on the choice.  *rows_out and *tpc_out
- * (either may be NULL) receive the shape in use.  Synchronises `stream`. */
-int dpso_batch_autotune(dpso_batch *b, int32_t *rows_out, int32_t *tpc_out, void *stream);
-/* Sets the 2-opt launch shape by hand (rows 32 / 30 / 24 / 16 / 8, tours per CTA
- * 1 / 2 / 4; both 0: the defaults for the longest member).  DPSO_ERR_ARG when
- * the shape does not fit in shared memory for the longest member, or the
- * batch's members lack the row-shifted cost copies the tiled kernel reads.
- * Results do not depend on the shape.  Synchronises the batch's stream. */
-int dpso_batch_set_two_opt_shape(dpso_batch *b, int32_t rows, int32_t tpc);
+/* Launch shape of the tiled 2-opt kernel: tile height (rows: 32 / 30 / 24 /
+ * 16 / 8), tours per CTA (1 / 2 / 4) and tiles of one tour in flight at once
+ * (1, or 2 with one tour per CTA: two 8-warp subgroups of a 16-warp CTA).
+ * All zero means the defaults for the longest tour of the batch. */
+typedef struct {
+    int32_t rows;
+    int32_t tours_per_cta;
+    int32_t tiles_in_flight;
+} dpso_two_opt_shape;
+
+/* Picks the 2-opt launch shape for this batch by timing every shape that fits
+ * on scratch copies of the members' current tours (at most 8 moves per tour
+ * each, so the probe costs a few passes; best called right after creation).
+ * Results do not depend on the choice.  *chosen (may be NULL) receives the
+ * shape in use.  Synchronises `stream`. */
+int dpso_batch_autotune(dpso_batch *b, dpso_two_opt_shape *chosen, void *stream);
+/* Sets the 2-opt launch shape by hand (NULL or all zero: the defaults).
+ * DPSO_ERR_ARG when the shape is not one of the above, does not fit in shared
+ * memory for the longest member, or the members lack the row-shifted cost
+ * copies the tiled kernel reads.  Results do not depend on the shape.
+ * Synchronises the batch's stream. */
+int dpso_batch_set_two_opt_shape(dpso_batch *b, const dpso_two_opt_shape *shape);
 void dpso_batch_destroy(dpso_batch *b);
 
 /*

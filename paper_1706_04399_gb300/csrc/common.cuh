@@ -205,6 +205,7 @@ struct TwoOptBatch {
     int rows;         // tile height of the tiled kernel (0: the default for max_n)
     unsigned int* queue;
     int tpc;          // tours per CTA of the tiled kernel (0: the default for max_n)
+    int tg;           // tile subgroups per tour of the tiled kernel (0: the default)
 };
 cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 
@@ -213,9 +214,11 @@ __host__ __device__ int shifted_ld(int n);
 size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages);
 int two_opt_tiled_rows(int n);  // default tile height, 0 when no height fits
 int two_opt_tiled_tpc(int n, int rows);  // default tours per CTA
-bool two_opt_tiled_fits(int n, int rows, int tpc);  // the shape's shared memory fits
+int two_opt_tiled_tg(int n, int rows, int tpc);  // default tiles in flight per tour
+int two_opt_tiled_ctas(int n, int rows, int tpc, int tg);  // resident CTAs per SM
+bool two_opt_tiled_fits(int n, int rows, int tpc, int tg);  // a valid shape that fits
 cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStream_t st);
-cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int tpc, int num_sms,
+cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int tpc, int tg, int num_sms,
                                  cudaStream_t st);
 cudaError_t launch_two_opt_general(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 

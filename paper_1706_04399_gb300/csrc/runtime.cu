@@ -786,16 +786,24 @@ void dpso_destroy(dpso_swarm* s) {
 }  // extern "C"
 
 struct dpso_batch {
+    // One persistent 2-opt launch per class of members sharing a launch shape.
+    struct TwoOptClass {
+        TwoOptTask* tasks = nullptr;  // device, the class's members by descending n
+        int* toff = nullptr;          // device, tour offsets (nprob + 1)
+        unsigned int* queue = nullptr;
+        TwoOptBatch tb{};
+    };
     int device = 0, num_sms = 0;
     std::vector<dpso_swarm*> members;
     SwarmDesc* desc = nullptr;  // device, members in creation order
     int* off = nullptr;         // device, ninst + 1
-    TwoOptTask* tasks = nullptr;  // device, members by descending n
-    int* toff = nullptr;          // device, ninst + 1
-    unsigned int* queue = nullptr;
     BatchView bv{};
-    TwoOptBatch tb{};
     bool any_two_opt = false;
+    bool shifted = true;                 // every exchanging member has the shifted copies
+    std::vector<TwoOptTask> tasks;       // host: every exchanging member, by descending n
+    std::vector<TwoOptClass> cls;
+    std::vector<cudaStream_t> side;      // capture streams of the classes after the first
+    std::vector<cudaEvent_t> ev;         // fork, then one join per side stream
     cudaStream_t cap = nullptr;
     cudaGraphExec_t graph = nullptr;
     cudaStream_t last = nullptr;
@@ -803,14 +811,139 @@ struct dpso_batch {
 
 namespace {
 
+void free_classes(dpso_batch* b) {
+    for (auto& c : b->cls) {
+        void* bufs[] = {c.tasks, c.toff, c.queue};
+        for (void* p : bufs)
+            if (p) cudaFree(p);
+    }
+    b->cls.clear();
+}
+
 void free_batch(dpso_batch* b) {
     if (!b) return;
     if (b->graph) cudaGraphExecDestroy(b->graph);
-    void* bufs[] = {b->desc, b->off, b->tasks, b->toff, b->queue};
+    free_classes(b);
+    void* bufs[] = {b->desc, b->off};
     for (void* p : bufs)
         if (p) cudaFree(p);
+    for (cudaStream_t s : b->side) cudaStreamDestroy(s);
+    for (cudaEvent_t e : b->ev) cudaEventDestroy(e);
     if (b->cap) cudaStreamDestroy(b->cap);
     delete b;
+}
+
+// Default launch shape of the tiled kernel for tours of n viewpoints and the
+// resident CTAs per SM it gets (all zero: the general kernel).
+struct ShapeKey {
+    int rows = 0, tpc = 0, tg = 0, ctas = 0;
+    bool operator==(const ShapeKey& o) const {
+        return rows == o.rows && tpc == o.tpc && tg == o.tg && ctas == o.ctas;
+    }
+};
+
+ShapeKey default_shape(int n, bool shifted) {
+    ShapeKey k;
+    if (!shifted || two_opt_tiled_rows(n) == 0) return k;
+    k.rows = two_opt_tiled_rows(n);
+    k.tpc = two_opt_tiled_tpc(n, k.rows);
+    k.tg = two_opt_tiled_tg(n, k.rows, k.tpc);
+    k.ctas = two_opt_tiled_ctas(n, k.rows, k.tpc, k.tg);
+    return k;
+}
+
+// Splits the exchanging members into launch classes: runs of members (by
+// descending n) whose default shape and resident CTAs per SM agree, each
+// launched with that shape; or one class with a pinned shape for all.
+int build_classes(dpso_batch* b, const dpso_two_opt_shape* pinned) {
+    free_classes(b);
+    const int nt = static_cast<int>(b->tasks.size());
+    std::vector<std::pair<int, int>> runs;  // [first, last) task ranges
+    std::vector<ShapeKey> keys;
+    for (int i = 0; i < nt; ++i) {
+        const ShapeKey k =
+            pinned ? ShapeKey{} : default_shape(b->tasks[i].n, b->tasks[i].Cs != nullptr);
+        if (i == 0 || !(k == keys.back())) {
+            runs.push_back({i, i + 1});
+            keys.push_back(k);
+        } else {
+            runs.back().second = i + 1;
+        }
+    }
+    for (size_t c = 0; c < runs.size(); ++c) {
+        dpso_batch::TwoOptClass cl;
+        const int first = runs[c].first, cnt = runs[c].second - runs[c].first;
+        std::vector<int> toff(1, 0);
+        int max_n = 0;
+        bool shifted = true;  // the tiled kernel needs every member's shifted copies
+        for (int i = first; i < first + cnt; ++i) {
+            toff.push_back(toff.back() + b->tasks[i].count);
+            max_n = std::max(max_n, b->tasks[i].n);
+            shifted = shifted && b->tasks[i].Cs != nullptr;
+        }
+        int st = DPSO_OK;
+        if ((st = dalloc(&cl.tasks, cnt, b->last)) || (st = dalloc(&cl.toff, cnt + 1, b->last)) ||
+            (st = dalloc(&cl.queue, 1, b->last))) {
+            b->cls.push_back(cl);
+            return st;
+        }
+        b->cls.push_back(cl);
+        CK(cudaMemcpyAsync(cl.tasks, b->tasks.data() + first, sizeof(TwoOptTask) * cnt,
+                           cudaMemcpyHostToDevice, b->last));
+        CK(cudaMemcpyAsync(cl.toff, toff.data(), sizeof(int) * (cnt + 1), cudaMemcpyHostToDevice,
+                           b->last));
+        CK(cudaStreamSynchronize(b->last));  // the host vectors go out of scope
+        TwoOptBatch& tb = b->cls.back().tb;
+        tb = TwoOptBatch{cl.tasks, cl.toff, cnt, toff.back(), max_n, shifted, 0, cl.queue};
+        if (pinned) {
+            tb.rows = pinned->rows;
+            tb.tpc = pinned->tours_per_cta;
+            tb.tg = pinned->tiles_in_flight;
+        } else if (keys[c].rows > 0) {
+            tb.rows = keys[c].rows;
+            tb.tpc = keys[c].tpc;
+            tb.tg = keys[c].tg;
+        }
+    }
+    // one capture stream and one join event per class after the first
+    while (b->side.size() + 1 < b->cls.size()) {
+        cudaStream_t s = nullptr;
+        CK(cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking));
+        b->side.push_back(s);
+    }
+    while (b->ev.size() < b->cls.size()) {
+        cudaEvent_t e = nullptr;
+        CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        b->ev.push_back(e);
+    }
+    return DPSO_OK;
+}
+
+// One generation of every member: the particle update, mutation, gbest, the
+// exchange order, then the classes' 2-opt launches side by side (forked from
+// and joined back into `st`), then the second gbest pass.
+cudaError_t enqueue_batch_classes(dpso_batch* b, cudaStream_t st) {
+    cudaError_t e = launch_move(b->bv, st);
+    if (e == cudaSuccess) e = launch_mutation(b->bv, st);
+    if (e == cudaSuccess) e = launch_gbest(b->bv, 0, st);
+    if (e != cudaSuccess || !b->any_two_opt) return e;
+    e = launch_rank_cost(b->bv, st);
+    if (e == cudaSuccess && b->cls.size() > 1) e = cudaEventRecord(b->ev[0], st);
+    for (size_t c = 1; c < b->cls.size() && e == cudaSuccess; ++c) {
+        cudaStream_t s = b->side[c - 1];
+        e = cudaStreamWaitEvent(s, b->ev[0], 0);
+        if (e == cudaSuccess) e = cudaMemsetAsync(b->cls[c].queue, 0, sizeof(unsigned int), s);
+        if (e == cudaSuccess) e = launch_two_opt(b->cls[c].tb, b->num_sms, s);
+        if (e == cudaSuccess) e = cudaEventRecord(b->ev[c], s);
+    }
+    if (e == cudaSuccess && !b->cls.empty()) {
+        e = cudaMemsetAsync(b->cls[0].queue, 0, sizeof(unsigned int), st);
+        if (e == cudaSuccess) e = launch_two_opt(b->cls[0].tb, b->num_sms, st);
+    }
+    for (size_t c = 1; c < b->cls.size() && e == cudaSuccess; ++c)
+        e = cudaStreamWaitEvent(st, b->ev[c], 0);
+    if (e == cudaSuccess) e = launch_gbest(b->bv, 1, st);
+    return e;
 }
 
 int capture_batch(dpso_batch* b) {
@@ -820,8 +953,7 @@ int capture_batch(dpso_batch* b) {
     }
     cudaGraph_t g = nullptr;
     CK(cudaStreamBeginCapture(b->cap, cudaStreamCaptureModeRelaxed));
-    const cudaError_t e =
-        enqueue_batch_generation(b->bv, b->tb, b->any_two_opt, true, b->num_sms, b->cap);
+    const cudaError_t e = enqueue_batch_classes(b, b->cap);
     const cudaError_t e2 = cudaStreamEndCapture(b->cap, &g);
     if (e != cudaSuccess || e2 != cudaSuccess) {
         if (g) cudaGraphDestroy(g);
@@ -830,6 +962,103 @@ int capture_batch(dpso_batch* b) {
     const cudaError_t e3 = cudaGraphInstantiate(&b->graph, g, 0);
     cudaGraphDestroy(g);
     return e3 == cudaSuccess ? DPSO_OK : DPSO_ERR_CUDA;
+}
+
+// Times every shape that fits a class on scratch copies of its tours (gates
+// ignored, at most kProbeMoves moves per tour) and keeps the fastest.
+int autotune_class(dpso_batch* b, dpso_batch::TwoOptClass& cl, cudaStream_t st) {
+    constexpr int kProbeMoves = 8;
+    if (cl.tb.nprob <= 0 || !cl.tb.shifted || two_opt_tiled_rows(cl.tb.max_n) == 0)
+        return DPSO_OK;
+    std::vector<TwoOptTask> tasks(cl.tb.nprob);
+    CK(cudaMemcpy(tasks.data(), cl.tasks, sizeof(TwoOptTask) * cl.tb.nprob,
+                  cudaMemcpyDeviceToHost));
+    const std::vector<TwoOptTask> orig = tasks;
+    std::vector<void*> scratch;
+    TwoOptTask* dtasks = nullptr;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    auto cleanup = [&](int code) {
+        cudaStreamSynchronize(st);
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
+        if (dtasks) cudaFree(dtasks);
+        for (void* p : scratch) cudaFree(p);
+        return code;
+    };
+    int st2 = DPSO_OK;
+    for (TwoOptTask& t : tasks) {
+        uint16_t* tours = nullptr;
+        long long* cost = nullptr;
+        unsigned long long* cnt = nullptr;
+        int* status = nullptr;
+        if ((st2 = dalloc(&tours, static_cast<size_t>(t.count) * t.ldt, st)) ||
+            (st2 = dalloc(&cost, t.count, st)) || (st2 = dalloc(&cnt, 2, st)) ||
+            (st2 = dalloc(&status, 1, st)))
+            return cleanup(st2);
+        scratch.insert(scratch.end(), {tours, cost, cnt, status});
+        t.tours = tours;
+        t.cost = cost;
+        t.pbest = nullptr;
+        t.pcost = nullptr;
+        t.gate = nullptr;
+        t.pairs = cnt;
+        t.moves = cnt + 1;
+        t.status = status;
+        t.max_moves = kProbeMoves;
+        t.order = nullptr;
+    }
+    if ((st2 = dalloc(&dtasks, tasks.size(), st))) return cleanup(st2);
+    if (cudaMemcpyAsync(dtasks, tasks.data(), sizeof(TwoOptTask) * tasks.size(),
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess || cudaEventCreate(&e0) != cudaSuccess ||
+        cudaEventCreate(&e1) != cudaSuccess)
+        return cleanup(DPSO_ERR_CUDA);
+    float best = 1e30f;
+    int rows_b = 0, tpc_b = 0, tg_b = 0;
+    constexpr int kShapes[4][2] = {{1, 1}, {2, 1}, {4, 1}, {1, 2}};  // (tours per CTA, tiles)
+    for (int rows : {32, 30, 24, 16, 8}) {
+        for (const auto& sh : kShapes) {
+            const int tpc = sh[0], tg = sh[1];
+            if (!two_opt_tiled_fits(cl.tb.max_n, rows, tpc, tg)) continue;
+            for (size_t i = 0; i < tasks.size(); ++i) {  // restore the tours
+                if (cudaMemcpy2DAsync(tasks[i].tours, sizeof(uint16_t) * tasks[i].ldt,
+                                      orig[i].tours, sizeof(uint16_t) * orig[i].ldt,
+                                      sizeof(uint16_t) * tasks[i].n, tasks[i].count,
+                                      cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+                    cudaMemcpyAsync(tasks[i].cost, orig[i].cost,
+                                    sizeof(long long) * tasks[i].count, cudaMemcpyDeviceToDevice,
+                                    st) != cudaSuccess)
+                    return cleanup(DPSO_ERR_CUDA);
+            }
+            TwoOptBatch tb = cl.tb;
+            tb.tasks = dtasks;
+            if (cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st) != cudaSuccess ||
+                cudaEventRecord(e0, st) != cudaSuccess)
+                return cleanup(DPSO_ERR_CUDA);
+            const cudaError_t le = launch_two_opt_tiled(tb, rows, tpc, tg, b->num_sms, st);
+            if (le == cudaErrorInvalidValue || le == cudaErrorInvalidConfiguration) {
+                cudaGetLastError();  // this shape does not fit: skip it
+                continue;
+            }
+            float ms = 0.f;
+            if (le != cudaSuccess || cudaEventRecord(e1, st) != cudaSuccess ||
+                cudaEventSynchronize(e1) != cudaSuccess ||
+                cudaEventElapsedTime(&ms, e0, e1) != cudaSuccess)
+                return cleanup(DPSO_ERR_CUDA);
+            if (ms < best) {
+                best = ms;
+                rows_b = rows;
+                tpc_b = tpc;
+                tg_b = tg;
+            }
+        }
+    }
+    if (rows_b > 0) {
+        cl.tb.rows = rows_b;
+        cl.tb.tpc = tpc_b;
+        cl.tb.tg = tg_b;
+    }
+    return cleanup(DPSO_OK);
 }
 
 }  // namespace
@@ -858,53 +1087,38 @@ int dpso_batch_create(dpso_batch** out, dpso_swarm* const* swarms, int32_t count
         return fail(DPSO_ERR_CUDA);
     std::vector<SwarmDesc> desc(count);
     std::vector<int> off(count + 1, 0);
-    int max_ldn = 0, max_n = 0, arrays = 5;
-    bool shifted = true;
+    int max_ldn = 0, max_S = 0, arrays = 5;
     for (int i = 0; i < count; ++i) {
         const dpso_swarm* s = swarms[i];
         desc[i].k = s->k;
         desc[i].d = s->d;
         off[i + 1] = off[i] + s->k.S;
         max_ldn = std::max(max_ldn, s->k.ldn);
-        max_n = std::max(max_n, s->k.n);
+        max_S = std::max(max_S, s->k.S);
         arrays = std::max(arrays, swarm_arrays(s->k));
-        shifted = shifted && s->Cs != nullptr;
-        b->any_two_opt = b->any_two_opt || (s->k.flags & DPSO_FLAG_TWO_OPT);
     }
-    // 2-opt work queue in order of decreasing tour length: long tours start first
+    // exchanging members by decreasing tour length: long tours start first
     std::vector<int> order(count);
     for (int i = 0; i < count; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(),
                      [&](int x, int y) { return swarms[x]->k.n > swarms[y]->k.n; });
-    std::vector<TwoOptTask> tasks;
-    std::vector<int> toff(1, 0);
     for (int i : order) {
         if (!(swarms[i]->k.flags & DPSO_FLAG_TWO_OPT)) continue;
-        tasks.push_back(swarm_task(swarms[i]));
-        toff.push_back(toff.back() + swarms[i]->k.S);
+        b->tasks.push_back(swarm_task(swarms[i]));
+        b->shifted = b->shifted && swarms[i]->Cs != nullptr;
     }
+    b->any_two_opt = !b->tasks.empty();
     int st = DPSO_OK;
-    const int nt = static_cast<int>(tasks.size());
-    if ((st = dalloc(&b->desc, count, b->last)) || (st = dalloc(&b->off, count + 1, b->last)) ||
-        (st = dalloc(&b->tasks, std::max(nt, 1), b->last)) ||
-        (st = dalloc(&b->toff, nt + 1, b->last)) || (st = dalloc(&b->queue, 1, b->last)))
+    if ((st = dalloc(&b->desc, count, b->last)) || (st = dalloc(&b->off, count + 1, b->last)))
         return fail(st);
-    if (cudaStreamSynchronize(b->last) != cudaSuccess) return fail(DPSO_ERR_CUDA);
-    if (cudaMemcpy(b->desc, desc.data(), sizeof(SwarmDesc) * count, cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaMemcpy(b->off, off.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        (nt > 0 && cudaMemcpy(b->tasks, tasks.data(), sizeof(TwoOptTask) * nt,
-                              cudaMemcpyHostToDevice) != cudaSuccess) ||
-        cudaMemcpy(b->toff, toff.data(), sizeof(int) * (nt + 1), cudaMemcpyHostToDevice) !=
-            cudaSuccess ||
-        cudaDeviceSynchronize() != cudaSuccess)
+    if (cudaMemcpyAsync(b->desc, desc.data(), sizeof(SwarmDesc) * count, cudaMemcpyHostToDevice,
+                        b->last) != cudaSuccess ||
+        cudaMemcpyAsync(b->off, off.data(), sizeof(int) * (count + 1), cudaMemcpyHostToDevice,
+                        b->last) != cudaSuccess ||
+        cudaStreamSynchronize(b->last) != cudaSuccess)
         return fail(DPSO_ERR_CUDA);
-    int max_S = 0;
-    for (int i = 0; i < count; ++i) max_S = std::max(max_S, swarms[i]->k.S);
     b->bv = BatchView{b->desc, b->off, count, off[count], max_ldn, arrays, max_S};
-    b->tb = TwoOptBatch{b->tasks, b->toff, nt, toff.back(), max_n, shifted, 0, b->queue};
-    b->any_two_opt = nt > 0;
+    if ((st = build_classes(b, nullptr))) return fail(st);
     if (cudaStreamCreateWithFlags(&b->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(DPSO_ERR_CUDA);
     if ((st = capture_batch(b))) return fail(st);
@@ -934,119 +1148,46 @@ int dpso_batch_step(dpso_batch* b, int32_t iterations, void* stream) {
     return DPSO_OK;
 }
 
-int dpso_batch_autotune(dpso_batch* b, int32_t* rows_out, int32_t* tpc_out, void* stream) {
+int dpso_batch_autotune(dpso_batch* b, dpso_two_opt_shape* chosen, void* stream) {
     if (!b) return DPSO_ERR_ARG;
     DeviceGuard g(b->device);
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     CK(cudaStreamSynchronize(b->last));
     b->last = st;
-    int chosen_rows = 0, chosen_tpc = 0;
-    if (b->tb.nprob > 0 && b->tb.shifted && two_opt_tiled_rows(b->tb.max_n) > 0) {
-        // Time every (tile height, tours per CTA) that fits on scratch copies
-        // of the members' current tours, the gates ignored and at most
-        // kProbeMoves moves per tour (a fixed amount of work per candidate);
-        // the choice cannot change results.
-        constexpr int kProbeMoves = 8;
-        std::vector<TwoOptTask> tasks(b->tb.nprob);
-        CK(cudaMemcpy(tasks.data(), b->tasks, sizeof(TwoOptTask) * b->tb.nprob,
-                      cudaMemcpyDeviceToHost));
-        const std::vector<TwoOptTask> orig = tasks;
-        std::vector<void*> scratch;
-        int st2 = DPSO_OK;
-        for (TwoOptTask& t : tasks) {
-            uint16_t* tours = nullptr;
-            long long* cost = nullptr;
-            unsigned long long* cnt = nullptr;
-            int* status = nullptr;
-            if ((st2 = dalloc(&tours, static_cast<size_t>(t.count) * t.ldt, st)) ||
-                (st2 = dalloc(&cost, t.count, st)) || (st2 = dalloc(&cnt, 2, st)) ||
-                (st2 = dalloc(&status, 1, st)))
-                break;
-            scratch.insert(scratch.end(), {tours, cost, cnt, status});
-            t.tours = tours;
-            t.cost = cost;
-            t.pbest = nullptr;
-            t.pcost = nullptr;
-            t.gate = nullptr;
-            t.pairs = cnt;
-            t.moves = cnt + 1;
-            t.status = status;
-            t.max_moves = kProbeMoves;
-            t.order = nullptr;
-        }
-        TwoOptTask* dtasks = nullptr;
-        if (!st2 && !(st2 = dalloc(&dtasks, tasks.size(), st))) {
-            CK(cudaMemcpyAsync(dtasks, tasks.data(), sizeof(TwoOptTask) * tasks.size(),
-                               cudaMemcpyHostToDevice, st));
-            CK(cudaStreamSynchronize(st));
-            cudaEvent_t e0, e1;
-            CK(cudaEventCreate(&e0));
-            CK(cudaEventCreate(&e1));
-            float best = 1e30f;
-            for (int rows : {32, 30, 24, 16, 8}) {
-                for (int tpc : {1, 2, 4}) {
-                    for (size_t i = 0; i < tasks.size(); ++i) {  // restore the tours
-                        CK(cudaMemcpy2DAsync(tasks[i].tours, sizeof(uint16_t) * tasks[i].ldt,
-                                             orig[i].tours, sizeof(uint16_t) * orig[i].ldt,
-                                             sizeof(uint16_t) * tasks[i].n, tasks[i].count,
-                                             cudaMemcpyDeviceToDevice, st));
-                        CK(cudaMemcpyAsync(tasks[i].cost, orig[i].cost,
-                                           sizeof(long long) * tasks[i].count,
-                                           cudaMemcpyDeviceToDevice, st));
-                    }
-                    TwoOptBatch tb = b->tb;
-                    tb.tasks = dtasks;
-                    CK(cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st));
-                    CK(cudaEventRecord(e0, st));
-                    const cudaError_t le = launch_two_opt_tiled(tb, rows, tpc, b->num_sms, st);
-                    if (le == cudaErrorInvalidValue || le == cudaErrorInvalidConfiguration) {
-                        cudaGetLastError();  // this shape does not fit: skip it
-                        continue;
-                    }
-                    CK(le);
-                    CK(cudaEventRecord(e1, st));
-                    CK(cudaEventSynchronize(e1));
-                    float ms = 0.f;
-                    CK(cudaEventElapsedTime(&ms, e0, e1));
-                    if (ms < best) {
-                        best = ms;
-                        chosen_rows = rows;
-                        chosen_tpc = tpc;
-                    }
-                }
-            }
-            cudaEventDestroy(e0);
-            cudaEventDestroy(e1);
-        }
-        CK(cudaStreamSynchronize(st));
-        if (dtasks) cudaFree(dtasks);
-        for (void* p : scratch) cudaFree(p);
-        if (st2) return st2;
-        if (chosen_rows > 0 && (chosen_rows != b->tb.rows || chosen_tpc != b->tb.tpc)) {
-            b->tb.rows = chosen_rows;
-            b->tb.tpc = chosen_tpc;
-            const int r = capture_batch(b);
-            if (r) return r;
+    for (auto& cl : b->cls) {
+        const int r = autotune_class(b, cl, st);
+        if (r) return r;
+    }
+    const int r = capture_batch(b);
+    if (r) return r;
+    if (chosen) {  // the shape of the class holding the longest tours
+        *chosen = dpso_two_opt_shape{0, 0, 0};
+        if (!b->cls.empty()) {
+            const TwoOptBatch& tb = b->cls[0].tb;
+            const int rows = tb.rows > 0 ? tb.rows : two_opt_tiled_rows(tb.max_n);
+            const int tpc = tb.tpc > 0 ? tb.tpc : (rows > 0 ? two_opt_tiled_tpc(tb.max_n, rows) : 0);
+            const int tg = tb.tg > 0 ? tb.tg : (rows > 0 ? two_opt_tiled_tg(tb.max_n, rows, tpc) : 0);
+            *chosen = dpso_two_opt_shape{rows, tpc, tg};
         }
     }
-    const int rows = b->tb.rows > 0 ? b->tb.rows : two_opt_tiled_rows(b->tb.max_n);
-    if (rows_out) *rows_out = rows;
-    if (tpc_out) *tpc_out = b->tb.tpc > 0 ? b->tb.tpc : (rows > 0 ? two_opt_tiled_tpc(b->tb.max_n, rows) : 0);
     return DPSO_OK;
 }
 
-int dpso_batch_set_two_opt_shape(dpso_batch* b, int32_t rows, int32_t tpc) {
+int dpso_batch_set_two_opt_shape(dpso_batch* b, const dpso_two_opt_shape* shape) {
     if (!b) return DPSO_ERR_ARG;
     DeviceGuard g(b->device);
-    if (rows == 0 && tpc == 0) {  // back to the defaults for the longest tour
-        b->tb.rows = 0;
-        b->tb.tpc = 0;
-    } else {
-        if (!b->tb.shifted || !two_opt_tiled_fits(b->tb.max_n, rows, tpc)) return DPSO_ERR_ARG;
-        b->tb.rows = rows;
-        b->tb.tpc = tpc;
+    const bool defaults =
+        !shape || (shape->rows == 0 && shape->tours_per_cta == 0 && shape->tiles_in_flight == 0);
+    if (!defaults) {
+        int max_n = 0;
+        for (const TwoOptTask& t : b->tasks) max_n = std::max(max_n, t.n);
+        if (!b->shifted || b->tasks.empty() ||
+            !two_opt_tiled_fits(max_n, shape->rows, shape->tours_per_cta, shape->tiles_in_flight))
+            return DPSO_ERR_ARG;
     }
     CK(cudaStreamSynchronize(b->last));
+    const int st = build_classes(b, defaults ? nullptr : shape);
+    if (st) return st;
     return capture_batch(b);
 }
 

@@ -245,7 +245,8 @@ cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     if (b.shifted && two_opt_tiled_rows(b.max_n) > 0) {
         const int rows = b.rows > 0 ? b.rows : two_opt_tiled_rows(b.max_n);
         const int tpc = b.tpc > 0 ? b.tpc : two_opt_tiled_tpc(b.max_n, rows);
-        return launch_two_opt_tiled(b, rows, tpc, num_sms, st);
+        const int tg = b.tg > 0 ? b.tg : two_opt_tiled_tg(b.max_n, rows, tpc);
+        return launch_two_opt_tiled(b, rows, tpc, tg, num_sms, st);
     }
     return launch_two_opt_general(b, num_sms, st);
 }

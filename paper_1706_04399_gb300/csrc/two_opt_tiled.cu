@@ -127,32 +127,58 @@ __device__ __forceinline__ void group_sync(int grp) {
     }
 }
 
+// Barrier over the 8 warps of tile subgroup `half` of a tour that two
+// subgroups share (TG = 2; the tour owns the whole CTA): named barrier
+// 1 + half.  With TG = 1 it is the tour's barrier.
+template <int TPC, int TG>
+__device__ __forceinline__ void half_sync(int grp, int half) {
+    if constexpr (TG == 1) {
+        group_sync<TPC>(grp);
+    } else if (half == 0) {
+        asm volatile("bar.sync 1, %0;\n" ::"n"(kThreads) : "memory");
+    } else {
+        asm volatile("bar.sync 2, %0;\n" ::"n"(kThreads) : "memory");
+    }
+}
+
 // ROWS: tile height (positions per tile, one per lane).  TPC: tours per CTA;
 // the 8 warps split into TPC groups of 8 / TPC warps, each solving its own
 // tour in its own slice of shared memory (`group_words` ints, 128-byte
 // aligned), so short tours still give every warp a long column range.
-template <int ROWS, int TPC>
-__global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
+// TG: tile subgroups per tour (TPC = 1 only): with TG = 2 the CTA has 16
+// warps and evaluates two tiles of the same pass at once, each 8-warp
+// subgroup with its own tile buffer and barrier, so a tour's passes take
+// about half as long (a shorter tail when tours need very different pass
+// counts) for the same shared memory and warps per SM as two CTAs.
+template <int ROWS, int TPC, int TG>
+__global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 : 3))
     two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
+    static_assert(TG == 1 || TPC == 1, "two tile subgroups need the whole CTA");
     constexpr int kRows = ROWS;        // positions per tile, one per lane
     constexpr int kStaged = ROWS + 1;  // cost rows staged per tile
-    constexpr int WPT = kWarps / TPC;  // warps per tour
-    constexpr int GT = WPT * 32;       // threads per tour
+    constexpr int WPT = kWarps * TG / TPC;  // warps per tour
+    constexpr int WSG = WPT / TG;           // warps per tile subgroup
+    constexpr int GT = WPT * 32;            // threads per tour
     // A group's shared slice seen through three element types (all alias its
-    // start): the tile buffer of kStaged x ldq ints, then the column records
+    // start): TG tile buffers of kStaged x ldq ints, then the column records
     // (n + 4 int2, the last four padding), then the tour (n + 1 uint16).
     // Offsets depend on the tour's n; slices are sized for the largest n.
     extern __shared__ __align__(128) int sm_all[];
-    __shared__ unsigned long long s_key[kWarps];
+    __shared__ unsigned long long s_key[kWarps * TG];
     __shared__ unsigned long long s_best[TPC];
     __shared__ int s_part[TPC], s_e0[TPC], s_e1[TPC];
     __shared__ long long s_pf[TPC];
-    __shared__ __align__(8) unsigned long long s_mbar[TPC];  // tile-arrival barrier per group
-    __shared__ int s_abort[TPC];  // a tile copy did not complete: the group stops
+    // tile-arrival barrier per tile subgroup; a subgroup whose tile copy did
+    // not complete sets its own abort flag (read by its own threads after its
+    // barrier, by the whole tour after a tour barrier)
+    __shared__ __align__(8) unsigned long long s_mbar[TPC * TG];
+    __shared__ int s_abort[TPC * TG];
 
     const int lane = threadIdx.x & 31;
     const int grp = (threadIdx.x >> 5) / WPT;  // tour group
     const int warp = (threadIdx.x >> 5) % WPT; // warp within the group
+    const int half = warp / WSG;               // tile subgroup within the tour
+    const int wsg = warp % WSG;                // warp within the tile subgroup
     const int tid = threadIdx.x % GT;          // thread within the group
     int* smi = sm_all + static_cast<size_t>(grp) * group_words;
     int2* smi2 = reinterpret_cast<int2*>(smi);
@@ -160,13 +186,20 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
     uint16_t* smu = reinterpret_cast<uint16_t*>(smi);
     unsigned long long* s_keyg = s_key + grp * WPT;
 
-    const unsigned mbar = smem_addr(&s_mbar[grp]);
+    const int sg = grp * TG + half;  // this thread's tile subgroup slot
+    const unsigned mbar = smem_addr(&s_mbar[sg]);
     unsigned phase = 0;  // parity of the tile-arrival phase to wait for
-    if (tid == 0) {
+    if (tid % (WSG * 32) == 0) {
         asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;\n" ::"r"(mbar) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
-        s_abort[grp] = 0;
+        s_abort[sg] = 0;
     }
+    auto tour_aborted = [&]() {  // after a tour barrier: uniform over the tour
+        bool ab = false;
+#pragma unroll
+        for (int h = 0; h < TG; ++h) ab = ab || s_abort[grp * TG + h] != 0;
+        return ab;
+    };
     for (;;) {
         if (tid == 0) s_part[grp] = static_cast<int>(atomicAdd(b.queue, 1u));
         group_sync<TPC>(grp);
@@ -182,7 +215,7 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
         const int n = a.n;
         const int ldq = shifted_ld(n);
         const int buf_words = kStaged * ldq;
-        const int rec2 = buf_words / 2;         // int2 index of record 0 (even)
+        const int rec2 = TG * buf_words / 2;    // int2 index of record 0 (even)
         const int xs16 = (rec2 + n + 4) * 4;    // uint16 index of x_0
         const int* __restrict__ C = a.C;
         const int ldc = a.ldc;
@@ -190,17 +223,17 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
         const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
         const int guard = 1000 + 100 * n;
 
-        // Warp 0 of the group stages the cost rows of the tile starting at I:
+        // Warp 0 of the subgroup stages the cost rows of the tile starting at I:
         // lane r posts row r as one bulk copy (row r from shifted copy
         // (r>>3)&3); lane 0 first arms the barrier with the tile's bytes.
         // Offsets into the shifted copies fit 32 bits (4 n ldq words < 2^30).
         const char* const cs0 = reinterpret_cast<const char*>(a.Cs);
-        const unsigned tile_s = smem_addr(smi);
+        const unsigned tile_s = smem_addr(smi + half * buf_words);
         const unsigned row_bytes = static_cast<unsigned>(ldq) * 4u;
         auto stage = [&](int I) {
             const int count = min(kStaged, n - 1 - I);
-            if (warp == 0) {
-                // the group barrier before this ordered the generic reads of
+            if (wsg == 0) {
+                // the subgroup barrier before this ordered the generic reads of
                 // the previous tile; this orders them before the async writes
                 asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
                 if (lane == 0)
@@ -227,7 +260,7 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
                     "selp.u32 %0, 1, 0, p; }\n"
                     : "=r"(done) : "r"(mbar), "r"(phase) : "memory");
                 if (!done && clock64() - t0 > (1ll << 32)) {
-                    s_abort[grp] = 1;
+                    s_abort[sg] = 1;
                     if (a.status) atomicExch(a.status, DPSO_ERR_TIMEOUT);
                     break;
                 }
@@ -256,24 +289,24 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
             }
             unsigned long long key = ~0ull;
             int ke0 = 0, ke1 = 0;
-            for (int t = 0; t < ntiles; ++t) {
+            for (int t = half; t < ntiles; t += TG) {
                 const int I = t * kRows;
-                group_sync<TPC>(grp);  // the previous tile is no longer read
-                if (s_abort[grp]) break;  // read after the barrier: the group agrees
+                half_sync<TPC, TG>(grp, half);  // the previous tile is no longer read
+                if (s_abort[sg]) break;  // read after the barrier: the subgroup agrees
                 stage(I);
                 stage_wait();
                 // lanes past the tile height idle on a valid row; byte offsets
                 // of this lane's two rows (row start plus its 0..3 word shift)
                 const int ra = min(lane, kRows - 1), rb1 = min(lane + 1, kRows);
-                const int p1 = ra * ldq + ((ra >> 3) & 3);
-                const int p2 = rb1 * ldq + ((rb1 >> 3) & 3);
+                const int p1 = half * buf_words + ra * ldq + ((ra >> 3) & 3);
+                const int p2 = half * buf_words + rb1 * ldq + ((rb1 >> 3) & 3);
                 const char* const r1 = reinterpret_cast<const char*>(smi + p1);
                 const char* const r2 = reinterpret_cast<const char*>(smi + p2);
                 // columns in groups of four, contiguous per warp; the records
                 // past n are padding
                 const int cbeg = I + 2;
                 const int ngroups = (n - cbeg + 3) >> 2;
-                const int g0 = (ngroups * warp) / WPT, g1 = (ngroups * (warp + 1)) / WPT;
+                const int g0 = (ngroups * wsg) / WSG, g1 = (ngroups * (wsg + 1)) / WSG;
                 // first valid column of this lane's row (rows past n-3 have none)
                 const int lim = (lane < kRows && I + lane <= n - 3) ? I + lane + 2 : INT_MAX;
                 int m = INT_MAX, cm = 0;
@@ -337,7 +370,7 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
             const unsigned long long kw = warp_min_u64(key);
             if (lane == 0) s_keyg[warp] = kw;
             group_sync<TPC>(grp);
-            if (s_abort[grp]) break;  // no move from a pass with a missing tile
+            if (tour_aborted()) break;  // no move from a pass with a missing tile
             if (warp == 0) {
                 unsigned long long kk = lane < WPT ? s_keyg[lane] : ~0ull;
                 kk = warp_min_u64(kk);
@@ -395,38 +428,41 @@ __global__ void __launch_bounds__(kThreads, ROWS == 30 ? 4 : 3)
             if (tid == 0) a.pcost[p] = f;
         }
         group_sync<TPC>(grp);
-        if (s_abort[grp]) break;  // copies are not completing: the group stops
+        if (tour_aborted()) break;  // copies are not completing: the group stops
     }
 }
 
-// Shared bytes of one tour group, rounded to 128 bytes.
-size_t group_bytes(int n, int rows) { return (two_opt_tiled_smem(n, rows, 1) + 127) / 128 * 128; }
+// Shared bytes of one tour group (TG tile buffers), rounded to 128 bytes.
+size_t group_bytes(int n, int rows, int tg) {
+    return (two_opt_tiled_smem(n, rows, tg) + 127) / 128 * 128;
+}
 
-template <int ROWS, int TPC>
+template <int ROWS, int TPC, int TG>
 cudaError_t launch_cfg(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
-    const size_t gb = group_bytes(b.max_n, ROWS);
+    const size_t gb = group_bytes(b.max_n, ROWS, TG);
     const size_t smem = gb * TPC;
-    cudaError_t e = cudaFuncSetAttribute(two_opt_tiled_kernel<ROWS, TPC>,
+    cudaError_t e = cudaFuncSetAttribute(two_opt_tiled_kernel<ROWS, TPC, TG>,
                                          cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two_opt_tiled_kernel<ROWS, TPC>,
-                                                      kThreads, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two_opt_tiled_kernel<ROWS, TPC, TG>,
+                                                      kThreads * TG, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = max(1, min((b.total + TPC - 1) / TPC, per_sm * num_sms));
-    two_opt_tiled_kernel<ROWS, TPC>
-        <<<grid, kThreads, smem, st>>>(b, static_cast<int>(gb / sizeof(int)));
+    two_opt_tiled_kernel<ROWS, TPC, TG>
+        <<<grid, kThreads * TG, smem, st>>>(b, static_cast<int>(gb / sizeof(int)));
     return cudaGetLastError();
 }
 
 template <int ROWS>
-cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int num_sms, cudaStream_t st) {
+cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int tg, int num_sms, cudaStream_t st) {
+    if (tg == 2) return tpc == 1 ? launch_cfg<ROWS, 1, 2>(b, num_sms, st) : cudaErrorInvalidValue;
     switch (tpc) {
-        case 1: return launch_cfg<ROWS, 1>(b, num_sms, st);
-        case 2: return launch_cfg<ROWS, 2>(b, num_sms, st);
-        case 4: return launch_cfg<ROWS, 4>(b, num_sms, st);
+        case 1: return launch_cfg<ROWS, 1, 1>(b, num_sms, st);
+        case 2: return launch_cfg<ROWS, 2, 1>(b, num_sms, st);
+        case 4: return launch_cfg<ROWS, 4, 1>(b, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }
@@ -434,10 +470,12 @@ cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int num_sms, cudaStream_t
 }  // namespace
 
 // Resident CTAs per SM for a shape: shared memory (228 KB per SM, 1 KB
-// reserved per CTA) against registers (64 per thread at R = 30, else 80).
-static int tiled_ctas_per_sm(int n, int rows, int tpc) {
-    const int by_smem = static_cast<int>((228 * 1024) / (group_bytes(n, rows) * tpc + 1024));
-    return min(by_smem, rows == 30 ? 4 : 3);
+// reserved per CTA) against registers (256-thread CTAs: 64 per thread at
+// R = 30, else 80; 512-thread CTAs: 64).
+int two_opt_tiled_ctas(int n, int rows, int tpc, int tg) {
+    const int by_smem =
+        static_cast<int>((228 * 1024) / (group_bytes(n, rows, tg) * tpc + 1024));
+    return min(by_smem, tg == 2 ? 2 : (rows == 30 ? 4 : 3));
 }
 
 // Default launch shape for tours of n viewpoints, from sweeps on GB300 of full
@@ -452,20 +490,27 @@ static int tiled_ctas_per_sm(int n, int rows, int tpc) {
 int two_opt_tiled_rows(int n) {
     if (n < 3 || n > 65535) return 0;
     if (n <= 128) return 32;
-    if (tiled_ctas_per_sm(n, 30, n <= 256 ? 2 : 1) >= 4) return 30;
+    if (two_opt_tiled_ctas(n, 30, n <= 256 ? 2 : 1, 1) >= 4) return 30;
     for (int rows : {32, 24, 16, 8}) {
         if (two_opt_tiled_smem(n, rows, 1) > 220 * 1024) continue;
-        if (rows == 32 && tiled_ctas_per_sm(n, 32, 1) == 1 &&
-            two_opt_tiled_smem(n, 24, 1) <= 220 * 1024 && tiled_ctas_per_sm(n, 24, 1) >= 2)
+        if (rows == 32 && two_opt_tiled_ctas(n, 32, 1, 1) == 1 &&
+            two_opt_tiled_smem(n, 24, 1) <= 220 * 1024 && two_opt_tiled_ctas(n, 24, 1, 1) >= 2)
             return 24;
         return rows;
     }
     return 0;
 }
 
+// Tiles of one tour in flight for the default shape: 2 for 30-row tiles with
+// one tour per CTA when two such 16-warp CTAs fit in an SM (measured on the
+// facade generation: 10.9 vs 11.6 ms), else 1.
+int two_opt_tiled_tg(int n, int rows, int tpc) {
+    return rows == 30 && tpc == 1 && two_opt_tiled_ctas(n, 30, 1, 2) >= 2 ? 2 : 1;
+}
+
 int two_opt_tiled_tpc(int n, int rows) {
     int tpc = n <= 128 ? 4 : (n <= 256 ? 2 : 1);
-    while (tpc > 1 && group_bytes(n, rows) * tpc > 220 * 1024) tpc /= 2;
+    while (tpc > 1 && group_bytes(n, rows, 1) * tpc > 220 * 1024) tpc /= 2;
     return tpc;
 }
 
@@ -475,21 +520,22 @@ cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStre
     return cudaGetLastError();
 }
 
-bool two_opt_tiled_fits(int n, int rows, int tpc) {
+bool two_opt_tiled_fits(int n, int rows, int tpc, int tg) {
     return n >= 3 && n <= 65535 &&
            (rows == 32 || rows == 30 || rows == 24 || rows == 16 || rows == 8) &&
-           (tpc == 1 || tpc == 2 || tpc == 4) && group_bytes(n, rows) * tpc <= 220 * 1024;
+           (tpc == 1 || tpc == 2 || tpc == 4) && (tg == 1 || (tg == 2 && tpc == 1)) &&
+           group_bytes(n, rows, tg) * tpc <= 220 * 1024;
 }
 
-cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int tpc, int num_sms,
+cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int tpc, int tg, int num_sms,
                                  cudaStream_t st) {
-    if (!b.shifted || !two_opt_tiled_fits(b.max_n, rows, tpc)) return cudaErrorInvalidValue;
+    if (!b.shifted || !two_opt_tiled_fits(b.max_n, rows, tpc, tg)) return cudaErrorInvalidValue;
     switch (rows) {
-        case 32: return launch_rows<32>(b, tpc, num_sms, st);
-        case 30: return launch_rows<30>(b, tpc, num_sms, st);
-        case 24: return launch_rows<24>(b, tpc, num_sms, st);
-        case 16: return launch_rows<16>(b, tpc, num_sms, st);
-        case 8: return launch_rows<8>(b, tpc, num_sms, st);
+        case 32: return launch_rows<32>(b, tpc, tg, num_sms, st);
+        case 30: return launch_rows<30>(b, tpc, tg, num_sms, st);
+        case 24: return launch_rows<24>(b, tpc, tg, num_sms, st);
+        case 16: return launch_rows<16>(b, tpc, tg, num_sms, st);
+        case 8: return launch_rows<8>(b, tpc, tg, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }

@@ -66,6 +66,11 @@ class dpso_timing(ctypes.Structure):
                 ("generations", ctypes.c_int32), ("reserved", ctypes.c_int32)]
 
 
+class dpso_two_opt_shape(ctypes.Structure):
+    _fields_ = [("rows", ctypes.c_int32), ("tours_per_cta", ctypes.c_int32),
+                ("tiles_in_flight", ctypes.c_int32)]
+
+
 class dpso_server_params(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_int32),
                 ("generations_per_tick", ctypes.c_int32)]
@@ -133,8 +138,9 @@ def lib():
             "dpso_batch_create": (ctypes.c_int, [ctypes.POINTER(_vp), ctypes.POINTER(_vp), _i32,
                                                  _vp]),
             "dpso_batch_step": (ctypes.c_int, [_vp, _i32, _vp]),
-            "dpso_batch_autotune": (ctypes.c_int, [_vp, _i32p, _i32p, _vp]),
-            "dpso_batch_set_two_opt_shape": (ctypes.c_int, [_vp, _i32, _i32]),
+            "dpso_batch_autotune": (ctypes.c_int, [_vp, ctypes.POINTER(dpso_two_opt_shape), _vp]),
+            "dpso_batch_set_two_opt_shape": (ctypes.c_int, [_vp,
+                                                            ctypes.POINTER(dpso_two_opt_shape)]),
             "dpso_batch_destroy": (None, [_vp]),
             "dpso_probe_l2_read_gbs": (ctypes.c_int, [ctypes.c_size_t, _i32,
                                                       ctypes.POINTER(ctypes.c_double), _vp]),
@@ -373,16 +379,16 @@ class Batch:
     def step(self, iterations: int, stream=None):
         _check(lib().dpso_batch_step(self._h, iterations, _stream(stream)), "dpso_batch_step")
 
-    def autotune(self, stream=None) -> tuple[int, int]:
-        """Chosen 2-opt launch shape: (tile height, tours per CTA)."""
-        rows = ctypes.c_int32(0)
-        tpc = ctypes.c_int32(0)
-        _check(lib().dpso_batch_autotune(self._h, ctypes.byref(rows), ctypes.byref(tpc),
-                                         _stream(stream)), "dpso_batch_autotune")
-        return rows.value, tpc.value
+    def autotune(self, stream=None) -> tuple[int, int, int]:
+        """Chosen 2-opt launch shape: (tile height, tours per CTA, tiles in flight)."""
+        sh = dpso_two_opt_shape()
+        _check(lib().dpso_batch_autotune(self._h, ctypes.byref(sh), _stream(stream)),
+               "dpso_batch_autotune")
+        return sh.rows, sh.tours_per_cta, sh.tiles_in_flight
 
-    def set_two_opt_shape(self, rows: int, tpc: int):
-        _check(lib().dpso_batch_set_two_opt_shape(self._h, rows, tpc),
+    def set_two_opt_shape(self, rows: int, tpc: int, tiles_in_flight: int = 1):
+        sh = dpso_two_opt_shape(rows, tpc, tiles_in_flight)
+        _check(lib().dpso_batch_set_two_opt_shape(self._h, ctypes.byref(sh)),
                "dpso_batch_set_two_opt_shape")
 
     def close(self):

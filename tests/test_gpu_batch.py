@@ -82,8 +82,8 @@ def test_batch_autotune_keeps_results_and_matches_oracle():
     Cs = [cost_matrix_gpu(inst) for inst, _, _ in members]
     swarms = [dpso.Swarm(C, inst.n, inst.tags, p, seed) for C, (inst, p, seed) in zip(Cs, members)]
     batch = dpso.Batch(swarms)
-    rows, tpc = batch.autotune()
-    assert rows in (32, 30, 24, 16, 8) and tpc in (1, 2, 4)
+    rows, tpc, tg = batch.autotune()
+    assert rows in (32, 30, 24, 16, 8) and tpc in (1, 2, 4) and tg in (1, 2)
     batch.step(5)
     for C, sw, (inst, p, seed) in zip(Cs, swarms, members):
         C_np, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
@@ -136,16 +136,16 @@ def test_every_two_opt_shape_gives_identical_states(rows):
         members.append((inst, dpso.default_params(swarm=S), 60 + k))
     Cs = [cost_matrix_gpu(inst) for inst, _, _ in members]
     want = [_solo_state(C, inst, p, seed, 6)[0] for C, (inst, p, seed) in zip(Cs, members)]
-    for tpc in (1, 2, 4):
+    for tpc, tg in ((1, 1), (2, 1), (4, 1), (1, 2)):
         swarms = [dpso.Swarm(C, inst.n, inst.tags, p, seed)
                   for C, (inst, p, seed) in zip(Cs, members)]
         batch = dpso.Batch(swarms)
-        batch.set_two_opt_shape(rows, tpc)
+        batch.set_two_opt_shape(rows, tpc, tg)
         batch.step(6)
         for sw, w, (inst, _, _) in zip(swarms, want, members):
             got = sw.state()
             for key in KEYS:
-                assert np.array_equal(got[key], w[key]), (rows, tpc, inst.n, key)
+                assert np.array_equal(got[key], w[key]), (rows, tpc, tg, inst.n, key)
         batch.close()
         for sw in swarms:
             sw.close()

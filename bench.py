@@ -474,7 +474,8 @@ def serving_line(args):
     _, w = stream_reqs[0]
     dpso.dpso_plan(w.xyz, w.boxes, w.tags, cp, params[0], w.seed, 1)
 
-    server = dpso.Server(dpso.default_server_params())
+    policy = dpso.SERVE_SHORTEST_FIRST if args.policy == "shortest" else dpso.SERVE_ARRIVAL_ORDER
+    server = dpso.Server(dpso.default_server_params(max_active=args.max_active, policy=policy))
     sampler = ClockSampler(gpu_index_for_smi(0))
     ids = []
     with sampler:
@@ -522,7 +523,8 @@ def serving_line(args):
                     "max_latency_s": float(lat.max()),
                     "one_per_launch_requests_per_s": len(stream_reqs) / solo_s,
                     "speedup": solo_s / served_s, "identical_tours": identical,
-                    "peak_active": sstats["peak_active"], "ticks": sstats["ticks"]},
+                    "peak_active": sstats["peak_active"], "ticks": sstats["ticks"],
+                    "policy": args.policy, "max_active": args.max_active},
         "gpu_launches": None, "roofline": None, "cpu_baseline": None,
         "e2e": {"value": units / served_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(np.mean([i.xyz.nbytes + i.boxes.nbytes + i.tags.nbytes
@@ -545,6 +547,9 @@ def main(argv=None):
     ap.add_argument("--instances", type=int, default=256, help="batched: instances")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests")
     ap.add_argument("--max-n", type=int, default=400, help="serving: largest request taken")
+    ap.add_argument("--policy", default="shortest", choices=["arrival", "shortest"],
+                    help="serving: admission order")
+    ap.add_argument("--max-active", type=int, default=16, help="serving: running requests at most")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)

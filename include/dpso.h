@@ -295,8 +295,9 @@ int dpso_plan(const double *xyz_host, int32_t n, const double *boxes_host, int32
  * for many requests at once; the paper has no server of its own).
  *
  * One engine thread per server, with its own CUDA stream on the device that
- * is current at creation.  Requests are copied at submission and queued in
- * arrival order.  Each engine tick admits queued requests while fewer than
+ * is current at creation.  Requests are copied at submission and queued;
+ * each engine tick admits queued requests (in the order `policy` sets) while
+ * fewer than
  * `max_active` are running and their estimated device footprint fits in
  * `memory_budget_bytes` (cost matrix by dpso_cost_matrix, swarm by
  * dpso_init; the state then stays on the device until the request ends),
@@ -309,10 +310,20 @@ int dpso_plan(const double *xyz_host, int32_t n, const double *boxes_host, int32
  */
 typedef struct dpso_server dpso_server;
 
+/* Admission order of queued requests: arrival, or least estimated work first
+ * (swarm x generation budget x n^3, the edge exchange's growth; ties by
+ * arrival).  The second lowers the latency of small requests in a burst and
+ * can delay large ones while smaller ones keep arriving.  Neither changes
+ * any result. */
+#define DPSO_SERVE_ARRIVAL_ORDER 0
+#define DPSO_SERVE_SHORTEST_FIRST 1
+
 typedef struct {
     uint64_t memory_budget_bytes; /* 0: half of the free device memory at creation */
     int32_t max_active;           /* running requests at most (default 64) */
     int32_t generations_per_tick; /* generations per engine tick at most (default 8) */
+    int32_t policy;               /* DPSO_SERVE_* (default arrival order) */
+    int32_t reserved;             /* must be 0 */
 } dpso_server_params;
 
 typedef struct {

@@ -42,6 +42,7 @@ struct Request {
     uint64_t seed = 0;
     int32_t iterations = 0;
     size_t footprint = 0;
+    double work = 0.0;  // admission estimate: swarm x budget x n^3
     Clock::time_point submitted;
     // results
     int status = 0;  // 0 queued/running, 1 done, < 0 DPSO_ERR_*
@@ -162,10 +163,16 @@ void engine_loop(dpso_server* sv) {
                 if (sv->queue.empty() ||
                     static_cast<int>(sv->active.size()) >= sv->prm.max_active)
                     break;
-                r = sv->queue.front();
+                // the next request: the oldest, or the one with the least
+                // estimated work (earliest submitted among equals)
+                auto pick = sv->queue.begin();
+                if (sv->prm.policy == DPSO_SERVE_SHORTEST_FIRST)
+                    for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it)
+                        if ((*it)->work < (*pick)->work) pick = it;
+                r = *pick;
                 never_fits = r->footprint > sv->prm.memory_budget_bytes;
                 if (!never_fits && sv->used + r->footprint > sv->prm.memory_budget_bytes) break;
-                sv->queue.pop_front();
+                sv->queue.erase(pick);
                 if (!never_fits) sv->used += r->footprint;
             }
             if (never_fits) {
@@ -266,10 +273,14 @@ void dpso_default_server_params(dpso_server_params* p) {
     p->memory_budget_bytes = 0;
     p->max_active = 64;
     p->generations_per_tick = 8;
+    p->policy = DPSO_SERVE_ARRIVAL_ORDER;
+    p->reserved = 0;
 }
 
 int dpso_server_create(dpso_server** out, const dpso_server_params* p) {
-    if (!out || !p || p->max_active < 1 || p->generations_per_tick < 1)
+    if (!out || !p || p->max_active < 1 || p->generations_per_tick < 1 ||
+        (p->policy != DPSO_SERVE_ARRIVAL_ORDER && p->policy != DPSO_SERVE_SHORTEST_FIRST) ||
+        p->reserved != 0)
         return DPSO_ERR_ARG;
     *out = nullptr;
     dpso_server* sv = new dpso_server();
@@ -326,6 +337,7 @@ int dpso_server_submit(dpso_server* sv, const dpso_request* r, int64_t* id) {
     q->seed = r->seed;
     q->iterations = r->iterations;
     q->footprint = request_footprint(r->n, r->m, r->params.swarm, r->iterations, r->params.flags);
+    q->work = static_cast<double>(r->params.swarm) * r->iterations * r->n * r->n * r->n;
     q->submitted = Clock::now();
     std::lock_guard<std::mutex> lock(sv->mu);
     q->id = sv->next_id++;

@@ -71,9 +71,14 @@ class dpso_two_opt_shape(ctypes.Structure):
                 ("tiles_in_flight", ctypes.c_int32)]
 
 
+SERVE_ARRIVAL_ORDER = 0
+SERVE_SHORTEST_FIRST = 1
+
+
 class dpso_server_params(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_int32),
-                ("generations_per_tick", ctypes.c_int32)]
+                ("generations_per_tick", ctypes.c_int32), ("policy", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
 
 
 class dpso_request(ctypes.Structure):

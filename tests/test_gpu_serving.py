@@ -157,3 +157,21 @@ def test_submit_rejects_bad_requests():
     with pytest.raises(dpso.DpsoError):
         server.poll(12345)
     server.close()
+
+
+def test_shortest_first_admission_keeps_results():
+    """Least-estimated-work-first admission with two slots: the small requests
+    (submitted last) are admitted before the large ones; every result is
+    still the solo run's."""
+    reqs = sorted(_requests(), key=lambda r: -r[0].n)[:6]  # largest first
+    server = dpso.Server(dpso.default_server_params(max_active=2, generations_per_tick=4,
+                                                    policy=dpso.SERVE_SHORTEST_FIRST))
+    ids = [server.submit(i.xyz, i.boxes, i.tags, cp, p, s, T) for i, cp, p, s, T in reqs]
+    got = _wait_all(server, ids)
+    for rid, req in zip(ids, reqs):
+        wt, wc = _solo(req)
+        assert got[rid][1] == wc and np.array_equal(got[rid][0], wt)
+    lat = {rid: server.poll(rid)[3] for rid in ids}
+    # the smallest request (submitted last) finished before the largest one
+    assert lat[ids[-1]] < lat[ids[0]]
+    server.close()

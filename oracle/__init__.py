@@ -25,6 +25,7 @@ _STAMP = _LIB + ".machine"
 DET_INIT = 1
 MUTATION = 2
 TWO_OPT = 4
+NODE_SWAP = 8   # with TWO_OPT: the exchange swaps two nodes instead of two edges
 ALL = DET_INIT | MUTATION | TWO_OPT
 
 ERR_ARG = -1
@@ -80,6 +81,8 @@ def lib():
         L.orc_boustrophedon.argtypes = [_i32p, ctypes.c_int32, ctypes.c_int32, _u16p]
         L.orc_two_opt.argtypes = [_i32p, ctypes.c_int32, _u16p, _i64p, ctypes.c_int32, _i64p]
         L.orc_two_opt.restype = ctypes.c_int64
+        L.orc_node_swap.argtypes = [_i32p, ctypes.c_int32, _u16p, _i64p, ctypes.c_int32, _i64p]
+        L.orc_node_swap.restype = ctypes.c_int64
         L.orc_swarm_new.argtypes = [
             _i32p, ctypes.c_int32, _i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
             ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -199,6 +202,17 @@ def two_opt(C, x, max_moves: int = 0):
     pairs = np.zeros(1, np.int64)
     mv = lib().orc_two_opt(_p(C, _i32p), C.shape[0], _p(y, _u16p), _p(f, _i64p),
                            max_moves, _p(pairs, _i64p))
+    return y, int(f[0]), int(mv), int(pairs[0])
+
+
+def node_swap(C, x, max_moves: int = 0):
+    """Node-swap exchange to convergence (best improvement). Returns (tour, cost, moves, pairs)."""
+    C = _c(C, np.int32)
+    y = _c(x, np.uint16).copy()
+    f = np.array([fitness(C, y)], np.int64)
+    pairs = np.zeros(1, np.int64)
+    mv = lib().orc_node_swap(_p(C, _i32p), C.shape[0], _p(y, _u16p), _p(f, _i64p),
+                             max_moves, _p(pairs, _i64p))
     return y, int(f[0]), int(mv), int(pairs[0])
 
 

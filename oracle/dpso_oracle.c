@@ -40,6 +40,7 @@
 #define ORC_DET_INIT 1
 #define ORC_MUTATION 2
 #define ORC_TWO_OPT 4
+#define ORC_NODE_SWAP 8 /* the exchange swaps two nodes instead of two edges */
 
 #define ORC_ERR_ARG (-1)
 #define ORC_ERR_RANGE (-2)
@@ -348,6 +349,70 @@ int64_t orc_two_opt(const int32_t *C, int32_t n, uint16_t *x, int64_t *f,
             x[lo] = x[hi];
             x[hi] = t;
         }
+        *f += best;
+        ++moves;
+    }
+    if (pairs_out)
+        *pairs_out += pairs;
+    return moves;
+}
+
+/* ------------------------------------------------------------------------ */
+/* Node-swap exchange (the "swap nodes(i,j) and evaluate fitness" reading of  */
+/* the exchange in the paper's GPU listing): every pair of positions i < j of */
+/* the cyclic tour is evaluated; the swap of x[i] and x[j] with the most      */
+/* improvement is applied; repeated until no swap improves.  Ties go to the   */
+/* smallest (i, j).  The change of a swap is the change of the edges that     */
+/* touch position i or j, each counted once (adjacent positions share one).   */
+/* Returns moves applied; *pairs_out grows by n(n-1)/2 per pass.              */
+/* ------------------------------------------------------------------------ */
+static int64_t swap_delta(const int32_t *C, int32_t n, const uint16_t *x, int32_t i, int32_t j)
+{
+    int32_t starts[4] = {(i - 1 + n) % n, i, (j - 1 + n) % n, j}; /* edge (k, k+1 mod n) */
+    int32_t uniq[4], nu = 0;
+    for (int q = 0; q < 4; ++q) {
+        int seen = 0;
+        for (int r = 0; r < nu; ++r)
+            seen |= uniq[r] == starts[q];
+        if (!seen)
+            uniq[nu++] = starts[q];
+    }
+    int64_t before = 0, after = 0;
+    for (int r = 0; r < nu; ++r) {
+        int32_t u = uniq[r], v = (uniq[r] + 1) % n;
+        before += C[(int64_t)x[u] * n + x[v]];
+        int32_t xu = u == i ? x[j] : (u == j ? x[i] : x[u]);
+        int32_t xv = v == i ? x[j] : (v == j ? x[i] : x[v]);
+        after += C[(int64_t)xu * n + xv];
+    }
+    return after - before;
+}
+
+int64_t orc_node_swap(const int32_t *C, int32_t n, uint16_t *x, int64_t *f,
+                      int32_t max_moves, int64_t *pairs_out)
+{
+    int64_t moves = 0, pairs = 0;
+    for (;;) {
+        if (max_moves > 0 && moves >= max_moves)
+            break;
+        int64_t best = 0;
+        int32_t bi = -1, bj = -1;
+        for (int32_t i = 0; i < n; ++i) {
+            for (int32_t j = i + 1; j < n; ++j) {
+                int64_t delta = swap_delta(C, n, x, i, j);
+                ++pairs;
+                if (delta < best) {
+                    best = delta;
+                    bi = i;
+                    bj = j;
+                }
+            }
+        }
+        if (bi < 0)
+            break;
+        uint16_t t = x[bi];
+        x[bi] = x[bj];
+        x[bj] = t;
         *f += best;
         ++moves;
     }
@@ -681,8 +746,12 @@ void orc_swarm_two_opt(orc_swarm *sw, const int32_t *idx, int32_t count)
     int32_t total = idx ? count : sw->S;
     for (int32_t r = 0; r < total; ++r) {
         int32_t p = idx ? idx[r] : r;
-        sw->moves += orc_two_opt(sw->C, sw->n, row_of(sw->X, sw->n, p), &sw->F[p],
-                                 sw->max_moves, &sw->pairs);
+        if (sw->flags & ORC_NODE_SWAP)
+            sw->moves += orc_node_swap(sw->C, sw->n, row_of(sw->X, sw->n, p), &sw->F[p],
+                                       sw->max_moves, &sw->pairs);
+        else
+            sw->moves += orc_two_opt(sw->C, sw->n, row_of(sw->X, sw->n, p), &sw->F[p],
+                                     sw->max_moves, &sw->pairs);
         pbest(sw, p);
     }
 }

@@ -372,6 +372,68 @@ def test_two_opt_optimality_and_moves(oracle_mod, n):
         assert np.array_equal(cur, y)
 
 
+def _swap_deltas_brute(oracle_mod, C, x):
+    """Change of the full recomputed tour length for swapping positions i < j."""
+    n = len(x)
+    f0 = oracle_mod.fitness(C, x)
+    D = np.full((n, n), np.iinfo(np.int64).max, np.int64)
+    for i in range(n):
+        for j in range(i + 1, n):
+            y = x.copy()
+            y[i], y[j] = y[j], y[i]
+            D[i, j] = oracle_mod.fitness(C, y) - f0
+    return D
+
+
+@pytest.mark.parametrize("n", [3, 4, 5, 6, 9, 23])
+def test_node_swap_optimality_and_moves(oracle_mod, n):
+    """Node-swap exchange: every applied swap is the lexicographic argmin of the
+    brute-force swap deltas (adjacent pairs and the wrap pair (0, n-1)
+    included), the output admits no improving swap, and each pass evaluates
+    n(n-1)/2 pairs."""
+    C = inputs.random_cost_matrix(n, 300 + n)
+    rng = np.random.default_rng(7 * n)
+    for _ in range(3):
+        x = rng.permutation(n).astype(np.uint16)
+        y, f, moves, pairs = oracle_mod.node_swap(C, x)
+        assert sorted(y.tolist()) == list(range(n))
+        assert f == oracle_mod.fitness(C, y)
+        assert _swap_deltas_brute(oracle_mod, C, y).min() >= 0
+        assert pairs == (moves + 1) * (n * (n - 1) // 2)
+        if n == 3:
+            assert moves == 0  # a swap only reverses a 3-cycle
+        cur = x.copy()
+        for _k in range(moves):
+            D = _swap_deltas_brute(oracle_mod, C, cur)
+            i, j = divmod(int(np.argmin(D)), n)
+            nxt, f2, m1, _ = oracle_mod.node_swap(C, cur, max_moves=1)
+            assert m1 == 1 and D[i, j] < 0
+            assert f2 - oracle_mod.fitness(C, cur) == D[i, j]
+            exp = cur.copy()
+            exp[i], exp[j] = exp[j], exp[i]
+            assert np.array_equal(nxt, exp)
+            cur = nxt
+        assert np.array_equal(cur, y)
+
+
+def test_node_swap_wrap_and_adjacent_pairs(oracle_mod):
+    """Points on a circle visited in order except two neighbours exchanged: the
+    only improving swap restores the order, whether the exchanged pair sits in
+    the middle of the array (adjacent positions) or at its two ends (the wrap
+    pair (0, n-1))."""
+    n = 12
+    ang = 2 * np.pi * np.arange(n) / n
+    xyz = np.stack([10 * np.cos(ang), 10 * np.sin(ang), np.zeros(n)], axis=1)
+    C, _ = oracle_mod.cost_matrix(xyz, np.zeros((0, 6)))
+    opt = oracle_mod.fitness(C, np.arange(n, dtype=np.uint16))
+    for i, j in ((4, 5), (0, n - 1)):
+        x = np.arange(n, dtype=np.uint16)
+        x[i], x[j] = x[j], x[i]
+        y, f, moves, _ = oracle_mod.node_swap(C, x, max_moves=1)
+        assert moves == 1 and f == opt
+        assert oracle_mod.fitness(C, y) == opt
+
+
 # ---------------------------------------------------------------- mutation
 
 def test_mutation_keeps_best_third_unchanged(oracle_mod):

@@ -36,7 +36,8 @@ sys.path.insert(0, ROOT)
 
 METRIC = "DPSO particle-iterations/s and 2-opt moves/s per GB300; batched p99 latency"
 UNIT = "particle-iterations/s"
-BYTES_PER_PAIR = 8          # C[x_i][x_j] + C[x_i+1][x_j+1], int32 each
+BYTES_PER_PAIR = 8          # 2-opt: C[x_i][x_j] + C[x_i+1][x_j+1], int32 each
+BYTES_PER_SWAP_PAIR = 16    # node swap: the four new edges' costs, int32 each
 CPU_SAMPLE_SWARM = 16       # oracle sample: particles
 CPU_SAMPLE_GENERATIONS = 10 # oracle sample: generations
 
@@ -77,12 +78,13 @@ def cpu_model() -> str:
 
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_sample(inst, swarm: int, warmup: int, generations: int):
+def oracle_sample(inst, swarm: int, warmup: int, generations: int, flags=None):
     """Times the oracle (single thread) on `generations` generations of a
     `swarm`-particle swarm over the same instance; returns (value, seconds)."""
     import oracle
     C, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
-    sw = oracle.Swarm(C, inst.tags, swarm=swarm, seed=inst.seed)
+    sw = oracle.Swarm(C, inst.tags, swarm=swarm, seed=inst.seed,
+                      flags=oracle.ALL if flags is None else flags)
     if warmup:
         sw.run(warmup)
     t0 = time.perf_counter()
@@ -259,7 +261,9 @@ def gpu_line(args):
     boxes = torch.from_numpy(inst.boxes).cuda()
     C = torch.empty((n, n), dtype=torch.int32, device="cuda")
     dpso.dpso_cost_matrix(xyz, n, boxes, inst.m, dpso.default_cost_params(), C, stream)
-    params = dpso.default_params(swarm=S)
+    node_swap = args.exchange == "node-swap"
+    flags = dpso.FLAGS_ALL | (dpso.FLAG_NODE_SWAP if node_swap else 0)
+    params = dpso.default_params(swarm=S, flags=flags)
     sw = dpso.Swarm(C, n, inst.tags, params, seed, stream)
     sw.set_timing(True)
     sw.step(args.warmup, stream)
@@ -301,10 +305,12 @@ def gpu_line(args):
         probes = {f"{mb}MiB": dpso.dpso_probe_l2_read_gbs(mb << 20, max(1, 960 // mb))
                   for mb in (8, 16, 24)}
         l2 = max(probes.values())
-        achieved = BYTES_PER_PAIR * pairs / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
-        traffic = two_opt_traffic(inst.name)
+        bpp = BYTES_PER_SWAP_PAIR if node_swap else BYTES_PER_PAIR
+        achieved = bpp * pairs / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
+        traffic = None if node_swap else two_opt_traffic(inst.name)
         roofline = {
-            "kernel": "two_opt_tiled_kernel", "bound": "l2", "achieved": achieved, "peak": l2,
+            "kernel": "node_swap_tiled_kernel" if node_swap else "two_opt_tiled_kernel",
+            "bound": "l2", "bytes_per_pair": bpp, "achieved": achieved, "peak": l2,
             "unit": "GB/s", "frac": achieved / l2 if l2 else None,
             "traffic": traffic,
             "peak_source": "L2 read bandwidth measured in this run by dpso_probe_l2_read_gbs "
@@ -316,7 +322,7 @@ def gpu_line(args):
         }
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cval, csec = oracle_sample(inst, CPU_SAMPLE_SWARM, 0, CPU_SAMPLE_GENERATIONS)
+            cval, csec = oracle_sample(inst, CPU_SAMPLE_SWARM, 0, CPU_SAMPLE_GENERATIONS, flags)
             cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
                    "sample": f"{inst.name} instance (n={n}), oracle swarm of {CPU_SAMPLE_SWARM} "
                              f"particles, first {CPU_SAMPLE_GENERATIONS} generations "
@@ -336,7 +342,7 @@ def gpu_line(args):
                                       ctypes.byref(cp), ctypes.byref(params), seed, args.steps,
                                       ctypes.cast(tour.data_ptr(), ctypes.POINTER(ctypes.c_int32)),
                                       ctypes.byref(cost))
-            e2e_s = time.perf_counter() - t0
+            e2e_s = time.perf_counter() - t0  # dpso_plan runs the same parameters
             if rc != 0:
                 raise dpso.DpsoError(rc, "dpso_plan")
             e2e = {"value": S * args.steps / e2e_s, "unit": UNIT,
@@ -350,7 +356,8 @@ def gpu_line(args):
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-            "config": {"workload": f"{inst.name}-{n}vp-{S}p", "n": n, "swarm": S,
+            "config": {"workload": f"{inst.name}-{n}vp-{S}p" + ("-nodeswap" if node_swap else ""),
+                       "n": n, "swarm": S, "exchange": args.exchange,
                        "generations_timed": args.steps, "boxes": inst.m,
                        "l2": "flushed between timed generations (256 MiB write)",
                        "parallelism": "replicas" if world > 1 else "single"},
@@ -550,6 +557,8 @@ def main(argv=None):
     ap.add_argument("--policy", default="shortest", choices=["arrival", "shortest"],
                     help="serving: admission order")
     ap.add_argument("--max-active", type=int, default=16, help="serving: running requests at most")
+    ap.add_argument("--exchange", default="2-opt", choices=["2-opt", "node-swap"],
+                    help="edge exchange of the swarm workloads")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)

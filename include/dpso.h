@@ -51,6 +51,11 @@ extern "C" {
 #define DPSO_FLAG_DET_INIT 1 /* Sec. 3.2.1 back-and-forth seeding (needs grid tags) */
 #define DPSO_FLAG_MUTATION 2 /* Sec. 3.2.2 random mutation */
 #define DPSO_FLAG_TWO_OPT 4  /* Sec. 3.2.3 edge exchange */
+/* With DPSO_FLAG_TWO_OPT: the exchange swaps two nodes (every pair of
+ * positions, the node-swap reading of the paper's GPU listing) instead of
+ * exchanging two edges.  Needs edge costs <= DPSO_NODE_SWAP_COST_MAX. */
+#define DPSO_FLAG_NODE_SWAP 8
+#define DPSO_NODE_SWAP_COST_MAX (1 << 28)
 
 /*
  * Swarm parameters (Fig. "pseudocode"; Sec. 4 uses w = 1, phi1 = phi2 = 0.4,
@@ -182,6 +187,21 @@ int dpso_two_opt(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t c
 int dpso_two_opt_noalloc(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t count,
                          int64_t *cost_dev, int32_t max_moves, int64_t *pairs_host,
                          int64_t *moves_host, void *stream);
+
+/*
+ * Node-swap exchange (the "swap nodes(i,j) and evaluate fitness" reading of
+ * the edge exchange in the paper's GPU listing, Sec. 3.2.3): for each of the
+ * `count` tours, repeatedly swap the two positions i < j (every pair of the
+ * cyclic tour) whose swap shortens the tour most, ties to the smallest
+ * (delta, i, j), until no swap improves or `max_moves` (> 0) swaps were made.
+ * Arguments, layout and errors as dpso_two_opt, except that entries of C must
+ * be at most DPSO_NODE_SWAP_COST_MAX (else DPSO_ERR_RANGE, as for n too large
+ * for a shared-memory tile); *pairs_host counts n(n-1)/2 per pass.
+ * Synchronises `stream`.
+ */
+int dpso_node_swap(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t count,
+                   int64_t *cost_dev, int32_t max_moves, int64_t *pairs_host,
+                   int64_t *moves_host, void *stream);
 
 /*
  * Creates a swarm over the n x n cost matrix C_dev (copied; the caller may free

@@ -29,6 +29,7 @@ SOURCES = {
     "swarm.cu": [],
     "two_opt.cu": [],
     "two_opt_tiled.cu": [],
+    "node_swap_tiled.cu": [],
     "runtime.cu": [],
     "two_opt_noalloc.cu": [],
     "probe.cu": [],

@@ -112,6 +112,8 @@ cudaError_t launch_cost_matrix(const double* xyz, int n, const double* boxes, in
 cudaError_t launch_check_inputs(const double* xyz, int n, const double* boxes, int m, int* err,
                                 cudaStream_t st);
 cudaError_t launch_check_cost(const int* C, int n, int ldc, int* err, cudaStream_t st);
+cudaError_t launch_check_cost_limit(const int* C, int n, int ldc, int limit, int* err,
+                                    cudaStream_t st);
 
 // One swarm as the generation kernels see it.
 struct SwarmDesc {
@@ -191,6 +193,7 @@ struct TwoOptTask {
     // (a permutation of 0..count-1); NULL means tour k.  Results do not depend
     // on it, only the time the last tour finishes does.
     const int* order;
+    int kind;  // exchange neighbourhood: 0 edge exchange (2-opt), 1 node swap
 };
 
 // One persistent launch over every tour of several problems: tasks[nprob] and
@@ -206,11 +209,18 @@ struct TwoOptBatch {
     unsigned int* queue;
     int tpc;          // tours per CTA of the tiled kernel (0: the default for max_n)
     int tg;           // tile subgroups per tour of the tiled kernel (0: the default)
+    int kind;         // exchange of every task: 0 edge exchange (2-opt), 1 node swap
 };
 cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 
 // ---- two_opt_tiled.cu: pipelined tiled variant (needs the shifted copies) ----
-__host__ __device__ int shifted_ld(int n);
+// Row pitch (words) of the shifted copies and of the staged rows: room for a
+// shift of up to 3 words, a multiple of 4 words (16-byte rows), ldq/4 odd.
+__host__ __device__ inline int shifted_ld(int n) {
+    int q = (n + 3 + 3) / 4 * 4;
+    if (((q / 4) & 1) == 0) q += 4;
+    return q;
+}
 size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages);
 int two_opt_tiled_rows(int n);  // default tile height, 0 when no height fits
 int two_opt_tiled_tpc(int n, int rows);  // default tours per CTA
@@ -221,6 +231,12 @@ cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStre
 cudaError_t launch_two_opt_tiled(const TwoOptBatch& b, int rows, int tpc, int tg, int num_sms,
                                  cudaStream_t st);
 cudaError_t launch_two_opt_general(const TwoOptBatch& b, int num_sms, cudaStream_t st);
+
+// ---- node_swap_tiled.cu: node-swap exchange (needs the shifted copies and
+// entries of C at most DPSO_NODE_SWAP_COST_MAX) ----
+size_t node_swap_tiled_smem(int n, int rows);
+int node_swap_tiled_rows(int n);  // 0 when no tile height fits
+cudaError_t launch_node_swap_tiled(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 
 // ---- runtime.cu ----
 __global__ void tours_valid_kernel(const uint16_t* tours, int n, int* err);

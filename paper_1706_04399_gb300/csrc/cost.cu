@@ -121,12 +121,12 @@ __global__ void check_inputs_kernel(const double* __restrict__ xyz, int n,
 }
 
 // Flags an asymmetric matrix or a non-zero diagonal (bit 0) and entries outside
-// [0, DPSO_COST_MAX] (bit 1).
-__global__ void check_cost_kernel(const int* __restrict__ C, int n, int ldc, int* err) {
+// [0, limit] (bit 1).
+__global__ void check_cost_kernel(const int* __restrict__ C, int n, int ldc, int limit, int* err) {
     const int i = blockIdx.y;
     for (int j = blockIdx.x * blockDim.x + threadIdx.x; j < n; j += gridDim.x * blockDim.x) {
         const int v = C[(size_t)i * ldc + j];
-        if (v < 0 || v > DPSO_COST_MAX) atomicOr(err, 2);
+        if (v < 0 || v > limit) atomicOr(err, 2);
         if (i == j ? v != 0 : v != C[(size_t)j * ldc + i]) atomicOr(err, 1);
     }
 }
@@ -149,8 +149,13 @@ cudaError_t launch_check_inputs(const double* xyz, int n, const double* boxes, i
 }
 
 cudaError_t launch_check_cost(const int* C, int n, int ldc, int* err, cudaStream_t st) {
+    return launch_check_cost_limit(C, n, ldc, DPSO_COST_MAX, err, st);
+}
+
+cudaError_t launch_check_cost_limit(const int* C, int n, int ldc, int limit, int* err,
+                                    cudaStream_t st) {
     dim3 grid((n + 255) / 256, n);
-    check_cost_kernel<<<grid, 256, 0, st>>>(C, n, ldc, err);
+    check_cost_kernel<<<grid, 256, 0, st>>>(C, n, ldc, limit, err);
     return cudaGetLastError();
 }
 

@@ -20,7 +20,7 @@ int validate_params(const dpso_params* p) {
     if (!unit(p->w) || !unit(p->phi1) || !unit(p->phi2)) return DPSO_ERR_ARG;
     if (p->swarm < 1 || p->mut_period < 1 || p->mut_swaps < 0 || p->det_frac_pct < 0 ||
         p->det_frac_pct > 100 || p->stall_limit < 0 || p->max_moves < 0 ||
-        p->two_opt_trigger < 0 || p->two_opt_trigger > 1 || (p->flags & ~7) != 0)
+        p->two_opt_trigger < 0 || p->two_opt_trigger > 1 || (p->flags & ~15) != 0)
         return DPSO_ERR_ARG;
     if (p->swarm > DPSO_MAX_SWARM) return DPSO_ERR_RANGE;
     return DPSO_OK;
@@ -151,6 +151,7 @@ TwoOptTask swarm_task(const dpso_swarm* s) {
     a.moves = &s->ctl->moves;
     a.status = &s->ctl->status;
     a.order = s->order;
+    a.kind = (s->k.flags & DPSO_FLAG_NODE_SWAP) ? 1 : 0;
     return a;
 }
 
@@ -161,8 +162,10 @@ BatchView swarm_view(const dpso_swarm* s) {
 }
 
 TwoOptBatch swarm_two_opt(const dpso_swarm* s) {
-    return TwoOptBatch{&s->meta->task, s->meta->toff, 1, s->k.S, s->k.n, s->Cs != nullptr, 0,
-                       &s->meta->queue};
+    TwoOptBatch tb{&s->meta->task, s->meta->toff, 1, s->k.S, s->k.n, s->Cs != nullptr, 0,
+                   &s->meta->queue};
+    tb.kind = (s->k.flags & DPSO_FLAG_NODE_SWAP) ? 1 : 0;
+    return tb;
 }
 
 // Generation kernels for a batch view; `with_mutation` false skips the
@@ -351,12 +354,18 @@ int dpso_fitness(const int32_t* C_dev, int32_t n, const uint16_t* tours_dev, int
     return DPSO_OK;
 }
 
-int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t count,
-                 int64_t* cost_dev, int32_t max_moves, int64_t* pairs_host, int64_t* moves_host,
-                 void* stream) {
+}  // extern "C"
+
+namespace {
+
+// dpso_two_opt and dpso_node_swap: validate, fitness, one persistent exchange
+// launch over `count` tours (kind 0: 2-opt, 1: node swap), counters back.
+int exchange_tours(int kind, const int32_t* C_dev, int32_t n, uint16_t* tours_dev,
+                   int32_t count, int64_t* cost_dev, int32_t max_moves, int64_t* pairs_host,
+                   int64_t* moves_host, void* stream) {
     if (!C_dev || !tours_dev || !cost_dev || n < 3 || count < 0 || max_moves < 0)
         return DPSO_ERR_ARG;
-    if (n > DPSO_MAX_N) return DPSO_ERR_RANGE;
+    if (n > DPSO_MAX_N || (kind == 1 && node_swap_tiled_rows(n) == 0)) return DPSO_ERR_RANGE;
     if (pairs_host) *pairs_host = 0;
     if (moves_host) *moves_host = 0;
     if (count == 0) return DPSO_OK;
@@ -383,7 +392,7 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
     Scratch host{};
     host.toff[1] = count;
     cudaError_t e = cudaMemcpyAsync(scratch, &host, sizeof(Scratch), cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess) e = launch_check_cost(C_dev, n, n, err, st);
+    if (e == cudaSuccess) e = launch_check_cost_limit(C_dev, n, n, kind ? DPSO_NODE_SWAP_COST_MAX : DPSO_COST_MAX, err, st);
     if (e == cudaSuccess) {
         tours_valid_kernel<<<count, 256, n, st>>>(tours_dev, n, err);
         e = cudaGetLastError();
@@ -395,7 +404,8 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
         if (cudaMallocAsync(&Cs, sizeof(int) * 4 * static_cast<size_t>(n) * shifted_ld(n), st) !=
             cudaSuccess) {
             cudaGetLastError();
-            Cs = nullptr;  // fall back to the kernel that stages rows itself
+            Cs = nullptr;  // 2-opt falls back to the kernel that stages rows itself
+            if (kind == 1) e = cudaErrorMemoryAllocation;
         } else {
             e = build_shifted_copies(C_dev, n, n, Cs, st);
         }
@@ -416,11 +426,13 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
         a.pairs = &scratch->pairs;
         a.moves = &scratch->moves;
         a.status = err;
+        a.kind = kind;
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(&scratch->task, &host.task, sizeof(TwoOptTask),
                                 cudaMemcpyHostToDevice, st);
-        const TwoOptBatch tb{&scratch->task, scratch->toff, 1, count, n, Cs != nullptr, 0,
-                             &scratch->queue};
+        TwoOptBatch tb{&scratch->task, scratch->toff, 1, count, n, Cs != nullptr, 0,
+                       &scratch->queue};
+        tb.kind = kind;
         if (e == cudaSuccess) e = launch_two_opt(tb, sms, st);
         if (e == cudaSuccess)
             e = cudaMemcpyAsync(counters, &scratch->pairs, sizeof(counters), cudaMemcpyDeviceToHost,
@@ -431,6 +443,7 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
     cudaFreeAsync(scratch, st);
     if (Cs) cudaFreeAsync(Cs, st);
     if (e == cudaSuccess) e = cudaStreamSynchronize(st);
+    if (e == cudaErrorMemoryAllocation) return DPSO_ERR_NO_MEMORY;
     if (e != cudaSuccess) return DPSO_ERR_CUDA;
     if (herr == DPSO_ERR_INTERNAL || herr == DPSO_ERR_TIMEOUT) return herr;
     if (herr & 1) return DPSO_ERR_ARG;
@@ -438,6 +451,24 @@ int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t c
     if (pairs_host) *pairs_host = static_cast<int64_t>(counters[0]);
     if (moves_host) *moves_host = static_cast<int64_t>(counters[1]);
     return DPSO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int dpso_two_opt(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t count,
+                 int64_t* cost_dev, int32_t max_moves, int64_t* pairs_host, int64_t* moves_host,
+                 void* stream) {
+    return exchange_tours(0, C_dev, n, tours_dev, count, cost_dev, max_moves, pairs_host,
+                          moves_host, stream);
+}
+
+int dpso_node_swap(const int32_t* C_dev, int32_t n, uint16_t* tours_dev, int32_t count,
+                   int64_t* cost_dev, int32_t max_moves, int64_t* pairs_host,
+                   int64_t* moves_host, void* stream) {
+    return exchange_tours(1, C_dev, n, tours_dev, count, cost_dev, max_moves, pairs_host,
+                          moves_host, stream);
 }
 
 int dpso_philox_draws(uint64_t seed, uint32_t phase, uint32_t iteration, uint32_t particle,
@@ -483,6 +514,8 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
         cudaSuccess)
         return fail(DPSO_ERR_CUDA);
     if (two_opt_rows(n) == 0) return fail(DPSO_ERR_RANGE);
+    const bool node_swap = (p->flags & DPSO_FLAG_TWO_OPT) && (p->flags & DPSO_FLAG_NODE_SWAP);
+    if (node_swap && node_swap_tiled_rows(n) == 0) return fail(DPSO_ERR_RANGE);
 
     Consts& k = s->k;
     k.n = n;
@@ -535,7 +568,9 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
     };
     if (cudaMemcpy2DAsync(s->C, sizeof(int) * k.ldc, C_dev, sizeof(int) * n, sizeof(int) * n, n,
                           cudaMemcpyDeviceToDevice, ust) != cudaSuccess ||
-        launch_check_cost(s->C, n, k.ldc, err, ust) != cudaSuccess)
+        launch_check_cost_limit(s->C, n, k.ldc,
+                                node_swap ? DPSO_NODE_SWAP_COST_MAX : DPSO_COST_MAX, err,
+                                ust) != cudaSuccess)
         return fail2(DPSO_ERR_CUDA);
     if (det) {
         s->n_det = static_cast<int>((static_cast<long long>(k.S) * p->det_frac_pct) / 100);
@@ -836,14 +871,19 @@ void free_batch(dpso_batch* b) {
 // Default launch shape of the tiled kernel for tours of n viewpoints and the
 // resident CTAs per SM it gets (all zero: the general kernel).
 struct ShapeKey {
-    int rows = 0, tpc = 0, tg = 0, ctas = 0;
+    int kind = 0, rows = 0, tpc = 0, tg = 0, ctas = 0;
     bool operator==(const ShapeKey& o) const {
-        return rows == o.rows && tpc == o.tpc && tg == o.tg && ctas == o.ctas;
+        return kind == o.kind && rows == o.rows && tpc == o.tpc && tg == o.tg && ctas == o.ctas;
     }
 };
 
-ShapeKey default_shape(int n, bool shifted) {
+ShapeKey default_shape(int n, bool shifted, int kind) {
     ShapeKey k;
+    k.kind = kind;
+    if (kind == 1) {  // node swap: one kernel shape per tile height
+        k.rows = node_swap_tiled_rows(n);
+        return k;
+    }
     if (!shifted || two_opt_tiled_rows(n) == 0) return k;
     k.rows = two_opt_tiled_rows(n);
     k.tpc = two_opt_tiled_tpc(n, k.rows);
@@ -861,8 +901,11 @@ int build_classes(dpso_batch* b, const dpso_two_opt_shape* pinned) {
     std::vector<std::pair<int, int>> runs;  // [first, last) task ranges
     std::vector<ShapeKey> keys;
     for (int i = 0; i < nt; ++i) {
-        const ShapeKey k =
-            pinned ? ShapeKey{} : default_shape(b->tasks[i].n, b->tasks[i].Cs != nullptr);
+        ShapeKey k;
+        if (pinned)
+            k.kind = b->tasks[i].kind;  // one class per exchange kind
+        else
+            k = default_shape(b->tasks[i].n, b->tasks[i].Cs != nullptr, b->tasks[i].kind);
         if (i == 0 || !(k == keys.back())) {
             runs.push_back({i, i + 1});
             keys.push_back(k);
@@ -895,7 +938,10 @@ int build_classes(dpso_batch* b, const dpso_two_opt_shape* pinned) {
         CK(cudaStreamSynchronize(b->last));  // the host vectors go out of scope
         TwoOptBatch& tb = b->cls.back().tb;
         tb = TwoOptBatch{cl.tasks, cl.toff, cnt, toff.back(), max_n, shifted, 0, cl.queue};
-        if (pinned) {
+        tb.kind = keys[c].kind;
+        if (keys[c].kind == 1) {
+            // node swap: the tile height follows max_n
+        } else if (pinned) {
             tb.rows = pinned->rows;
             tb.tpc = pinned->tours_per_cta;
             tb.tg = pinned->tiles_in_flight;
@@ -968,7 +1014,8 @@ int capture_batch(dpso_batch* b) {
 // ignored, at most kProbeMoves moves per tour) and keeps the fastest.
 int autotune_class(dpso_batch* b, dpso_batch::TwoOptClass& cl, cudaStream_t st) {
     constexpr int kProbeMoves = 8;
-    if (cl.tb.nprob <= 0 || !cl.tb.shifted || two_opt_tiled_rows(cl.tb.max_n) == 0)
+    if (cl.tb.kind != 0 || cl.tb.nprob <= 0 || !cl.tb.shifted ||
+        two_opt_tiled_rows(cl.tb.max_n) == 0)
         return DPSO_OK;
     std::vector<TwoOptTask> tasks(cl.tb.nprob);
     CK(cudaMemcpy(tasks.data(), cl.tasks, sizeof(TwoOptTask) * cl.tb.nprob,
@@ -1179,9 +1226,10 @@ int dpso_batch_set_two_opt_shape(dpso_batch* b, const dpso_two_opt_shape* shape)
     const bool defaults =
         !shape || (shape->rows == 0 && shape->tours_per_cta == 0 && shape->tiles_in_flight == 0);
     if (!defaults) {
-        int max_n = 0;
-        for (const TwoOptTask& t : b->tasks) max_n = std::max(max_n, t.n);
-        if (!b->shifted || b->tasks.empty() ||
+        int max_n = 0;  // the shape applies to the edge-exchange (2-opt) members
+        for (const TwoOptTask& t : b->tasks)
+            if (t.kind == 0) max_n = std::max(max_n, t.n);
+        if (!b->shifted || max_n == 0 ||
             !two_opt_tiled_fits(max_n, shape->rows, shape->tours_per_cta, shape->tiles_in_flight))
             return DPSO_ERR_ARG;
     }

@@ -242,6 +242,7 @@ cudaError_t launch_two_opt_general(const TwoOptBatch& b, int num_sms, cudaStream
 
 cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     if (b.total <= 0) return cudaSuccess;
+    if (b.kind == 1) return launch_node_swap_tiled(b, num_sms, st);
     if (b.shifted && two_opt_tiled_rows(b.max_n) > 0) {
         const int rows = b.rows > 0 ? b.rows : two_opt_tiled_rows(b.max_n);
         const int tpc = b.tpc > 0 ? b.tpc : two_opt_tiled_tpc(b.max_n, rows);

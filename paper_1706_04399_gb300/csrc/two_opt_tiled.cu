@@ -33,40 +33,12 @@
 //    never win, so only the triangle at the start of each tile is masked.
 #include <climits>
 
-#include "common.cuh"
+#include "tiled_common.cuh"
 
 namespace dpso {
 namespace {
 
-constexpr int kWarps = 8;
-constexpr int kThreads = kWarps * 32;
-
-__device__ __forceinline__ unsigned smem_addr(const void* p) {
-    return static_cast<unsigned>(__cvta_generic_to_shared(p));
-}
-
-// One row of `bytes` (a multiple of 16, both addresses 16-byte aligned) from
-// global to this CTA's shared memory by the bulk-copy engine; completion is
-// counted in bytes on the mbarrier at `mbar`.
-__device__ __forceinline__ void bulk_row(unsigned dst, const void* src, unsigned bytes,
-                                         unsigned mbar) {
-    asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n"
-        ::"r"(dst), "l"(src), "r"(bytes), "r"(mbar) : "memory");
-}
-
-// (delta, i, j) -> order-preserving 64-bit key: biased delta, then i, then j.
-__device__ __forceinline__ unsigned long long pack_key(int delta, int i, int j) {
-    return (static_cast<unsigned long long>(static_cast<uint32_t>(delta) ^ 0x80000000u) << 32) |
-           (static_cast<unsigned long long>(static_cast<uint32_t>(i)) << 16) |
-           static_cast<uint32_t>(j);
-}
-
-__device__ __forceinline__ unsigned long long warp_min_u64(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
-}
+using namespace tiled;
 
 // Builds copy k (k = 0..3) of C with every row shifted right by k words:
 // Cs[(k n + r) ldq + k + l] = C[r][l], zeros elsewhere.
@@ -81,14 +53,6 @@ __global__ void shift_copies_kernel(const int* __restrict__ C, int ldc, int n, i
 }
 
 }  // namespace
-
-// Row pitch (words) of the shifted copies and of the staged rows: room for a
-// shift of up to 3 words, a multiple of 4 words (16-byte rows), ldq/4 odd.
-__host__ __device__ int shifted_ld(int n) {
-    int q = (n + 3 + 3) / 4 * 4;
-    if (((q / 4) & 1) == 0) q += 4;
-    return q;
-}
 
 size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages) {
     const size_t rows =

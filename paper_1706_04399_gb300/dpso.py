@@ -29,7 +29,9 @@ COST_MAX = 1 << 29
 FLAG_DET_INIT = 1
 FLAG_MUTATION = 2
 FLAG_TWO_OPT = 4
+FLAG_NODE_SWAP = 8   # with FLAG_TWO_OPT: the exchange swaps nodes instead of edges
 FLAGS_ALL = FLAG_DET_INIT | FLAG_MUTATION | FLAG_TWO_OPT
+NODE_SWAP_COST_MAX = 1 << 28
 
 
 class DpsoError(RuntimeError):
@@ -123,6 +125,7 @@ def lib():
                                                 ctypes.POINTER(dpso_cost_params), _vp, _vp]),
             "dpso_fitness": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
             "dpso_two_opt": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p, _vp]),
+            "dpso_node_swap": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p, _vp]),
             "dpso_two_opt_noalloc": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p,
                                                     _vp]),
             "dpso_init": (ctypes.c_int, [ctypes.POINTER(_vp), _vp, _i32, _vp,
@@ -233,6 +236,16 @@ def dpso_two_opt(C_dev, n: int, tours_dev, count: int, cost_dev, max_moves: int 
     _check(lib().dpso_two_opt(_dev(C_dev), n, _dev(tours_dev), count, _dev(cost_dev), max_moves,
                               ctypes.byref(pairs), ctypes.byref(moves), _stream(stream)),
            "dpso_two_opt")
+    return pairs.value, moves.value
+
+
+def dpso_node_swap(C_dev, n: int, tours_dev, count: int, cost_dev, max_moves: int = 0,
+                   stream=None) -> tuple[int, int]:
+    pairs = ctypes.c_int64(0)
+    moves = ctypes.c_int64(0)
+    _check(lib().dpso_node_swap(_dev(C_dev), n, _dev(tours_dev), count, _dev(cost_dev), max_moves,
+                                ctypes.byref(pairs), ctypes.byref(moves), _stream(stream)),
+           "dpso_node_swap")
     return pairs.value, moves.value
 
 

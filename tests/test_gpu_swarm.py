@@ -179,7 +179,7 @@ def test_init_rejects_bad_arguments():
     inst = inputs.random_instance(12, 1, 9)
     C, C_np = _setup(inst)
     for kw in (dict(swarm=0), dict(w=1.5), dict(phi2=-0.1), dict(mut_period=0),
-               dict(two_opt_trigger=2), dict(flags=8)):
+               dict(two_opt_trigger=2), dict(flags=16)):
         with pytest.raises(dpso.DpsoError) as e:
             dpso.Swarm(C, inst.n, inst.tags, dpso.default_params(**kw), 1)
         assert e.value.status == dpso.ERR_ARG, kw

@@ -382,6 +382,12 @@ def _same_state(a: dict, b: dict) -> bool:
     return all(np.array_equal(a[k], b[k]) for k in keys) and (a["t"], a["gf"]) == (b["t"], b["gf"])
 
 
+def shard(items, rank: int, world: int):
+    """The items rank `rank` of `world` takes: every world-th, from its rank
+    (instances are independent, so no collective is needed)."""
+    return items[rank::world]
+
+
 def batched_line(args):
     """Independent instances of uneven size advanced together by dpso_batch_*
     (one set of launches per generation for all of them) against the same
@@ -391,8 +397,16 @@ def batched_line(args):
 
     from paper_1706_04399_gb300 import dpso, inputs
 
-    torch.cuda.set_device(0)
-    insts = inputs.batched()[: args.instances]
+    rank = _env_int("RANK", 0)
+    world = _env_int("WORLD_SIZE", 1)
+    local = _env_int("LOCAL_RANK", 0)
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    all_insts = inputs.batched()[: args.instances]
+    insts = shard(all_insts, rank, world)
     stream = torch.cuda.current_stream()
     Cs = []
     for inst in insts:
@@ -432,25 +446,39 @@ def batched_line(args):
         sw.step(args.warmup, stream)
     torch.cuda.synchronize()
     st0 = [sw.stats() for sw in together]
-    sampler = ClockSampler(gpu_index_for_smi(0))
+    sampler = ClockSampler(gpu_index_for_smi(local))
+    if dist:
+        dist.barrier()
     with sampler:
-        ms_batch = run(lambda: batch.step(1, stream), args.steps)
-        ms_solo = run(solo_step, args.steps)
+        ms_batch = max_over_ranks(run(lambda: batch.step(1, stream), args.steps), dist, "cuda")
+        if dist:
+            dist.barrier()
+        ms_solo = max_over_ranks(run(solo_step, args.steps), dist, "cuda")
     st1 = [sw.stats() for sw in together]
     identical = all(_same_state(a.state(), b.state()) for a, b in zip(together, alone))
     pairs = sum(b["two_opt_pairs"] - a["two_opt_pairs"] for a, b in zip(st0, st1))
-    value = S_total * args.steps / (ms_batch / 1e3)
-    solo_value = S_total * args.steps / (ms_solo / 1e3)
+    S_job = sum(i.swarm for i in all_insts)  # every rank's particles
+    value = S_job * args.steps / (ms_batch / 1e3)
+    solo_value = S_job * args.steps / (ms_solo / 1e3)
+    if dist:
+        t = torch.tensor([1.0 if identical else 0.0], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MIN)
+        identical = bool(t.item() == 1.0)
     batch.close()
     for sw in together + alone:
         sw.close()
-    ns = [i.n for i in insts]
+    if dist:
+        dist.destroy_process_group()
+    if rank != 0:
+        return None
+    ns = [i.n for i in all_insts]
     return {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_batch / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-        "config": {"workload": f"batched-{len(insts)}", "instances": len(insts),
-                   "n_min": min(ns), "n_max": max(ns), "swarm_total": S_total,
+        "config": {"workload": f"batched-{len(all_insts)}", "instances": len(all_insts),
+                   "parallelism": f"instances sharded over {world} GPU(s), no collective",
+                   "n_min": min(ns), "n_max": max(ns), "swarm_total": S_job,
                    "l2": "flushed between timed generations (256 MiB write)"},
         "batched": {"one_per_launch_value": solo_value, "speedup": value / solo_value,
                     "one_per_launch_ms_per_step": ms_solo / args.steps,

@@ -68,3 +68,33 @@ def test_reference_arm_line(monkeypatch):
     assert rc == 0 and line["impl"] == "reference" and line["value"] > 0
     assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+
+
+def _shard_rank(rank, world, port, out):
+    import torch.distributed as dist
+    os.environ.update(MASTER_ADDR="127.0.0.1", MASTER_PORT=str(port))
+    dist.init_process_group("gloo", rank=rank, world_size=world)
+    from paper_1706_04399_gb300 import inputs
+    mine = [inst.name for inst in bench.shard(inputs.batched(count=10), rank, world)]
+    gathered = [None] * world
+    dist.all_gather_object(gathered, mine)
+    out.put((rank, gathered))
+    dist.destroy_process_group()
+
+
+def test_instance_sharding_covers_every_instance_once():
+    ctx = torch.multiprocessing.get_context("spawn")
+    q = ctx.Queue()
+    port = 30500 + os.getpid() % 1000
+    procs = [ctx.Process(target=_shard_rank, args=(r, 3, port, q)) for r in range(3)]
+    for p in procs:
+        p.start()
+    got = [q.get(timeout=120) for _ in procs]
+    for p in procs:
+        p.join(timeout=120)
+        assert p.exitcode == 0
+    views = [g for _, g in got]
+    assert all(v == views[0] for v in views)          # every rank sees the same split
+    names = [n for part in views[0] for n in part]
+    assert sorted(names) == sorted(f"batched{i}" for i in range(10))  # each exactly once
+    assert [len(part) for part in views[0]] == [4, 3, 3]

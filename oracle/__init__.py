@@ -58,6 +58,7 @@ _i32p = ctypes.POINTER(ctypes.c_int32)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _f64p = ctypes.POINTER(ctypes.c_double)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def lib():
@@ -83,6 +84,13 @@ def lib():
         L.orc_two_opt.restype = ctypes.c_int64
         L.orc_node_swap.argtypes = [_i32p, ctypes.c_int32, _u16p, _i64p, ctypes.c_int32, _i64p]
         L.orc_node_swap.restype = ctypes.c_int64
+        L.orc_voxel_occupancy.argtypes = [_f64p, ctypes.c_double, _i32p, _f64p, ctypes.c_int32,
+                                          ctypes.c_int32, _u8p]
+        L.orc_voxel_occupancy.restype = ctypes.c_int
+        L.orc_cost_matrix_astar.argtypes = [_f64p, ctypes.c_int32, _u8p, _f64p, ctypes.c_double,
+                                            _i32p, _i32p, ctypes.c_int32, ctypes.c_int32,
+                                            ctypes.c_int32, _i32p]
+        L.orc_cost_matrix_astar.restype = ctypes.c_int
         L.orc_swarm_new.argtypes = [
             _i32p, ctypes.c_int32, _i32p, ctypes.c_int32, ctypes.c_double, ctypes.c_double,
             ctypes.c_double, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, ctypes.c_int32,
@@ -203,6 +211,39 @@ def two_opt(C, x, max_moves: int = 0):
     mv = lib().orc_two_opt(_p(C, _i32p), C.shape[0], _p(y, _u16p), _p(f, _i64p),
                            max_moves, _p(pairs, _i64p))
     return y, int(f[0]), int(mv), int(pairs[0])
+
+
+def voxel_occupancy(origin, voxel: float, dims, boxes, r2: int):
+    """Inflated occupancy of the voxel grid (Sec. 2.2): uint8 [nz, ny, nx]."""
+    o = _c(origin, np.float64)
+    d = _c(dims, np.int32)
+    b = _c(np.asarray(boxes, np.float64).reshape(-1, 6), np.float64)
+    occ = np.zeros((int(d[2]), int(d[1]), int(d[0])), np.uint8)
+    st = lib().orc_voxel_occupancy(_p(o, ctypes.POINTER(ctypes.c_double)), voxel, _p(d, _i32p),
+                                   _p(b, ctypes.POINTER(ctypes.c_double)), b.shape[0], r2,
+                                   _p(occ, ctypes.POINTER(ctypes.c_uint8)))
+    if st:
+        raise ValueError(f"voxel_occupancy rejected its arguments ({st})")
+    return occ
+
+
+def cost_matrix_astar(xyz, occ, origin, voxel: float, dims, weights=(1, 1, 1), unit_mm: int = 500,
+                      blocked_cost: int = 100_000_000, max_expansions: int = 100_000):
+    """A* edge costs (Sec. 2.2) over an occupancy grid; returns (C int32 [n, n], status)."""
+    x = _c(np.asarray(xyz, np.float64).reshape(-1, 3), np.float64)
+    n = x.shape[0]
+    oc = _c(occ, np.uint8)
+    o = _c(origin, np.float64)
+    d = _c(dims, np.int32)
+    a = _c(weights, np.int32)
+    C = np.zeros((n, n), np.int32)
+    f64 = ctypes.POINTER(ctypes.c_double)
+    st = lib().orc_cost_matrix_astar(_p(x, f64), n, _p(oc, ctypes.POINTER(ctypes.c_uint8)),
+                                     _p(o, f64), voxel, _p(d, _i32p), _p(a, _i32p), unit_mm,
+                                     blocked_cost, max_expansions, _p(C, _i32p))
+    if st == ERR_ARG:
+        raise ValueError("cost_matrix_astar rejected its arguments")
+    return C, int(st)
 
 
 def node_swap(C, x, max_moves: int = 0):

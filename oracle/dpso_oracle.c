@@ -175,6 +175,234 @@ int orc_cost_matrix(const double *xyz, int32_t n, const double *boxes, int32_t m
     return status;
 }
 
+/* ------------------------------------------------------------------------ */
+/* Sec. 2.2 edge costs by A* over a voxel grid (the alternative to the       */
+/* straight segments above).  The grid is given: origin (m), voxel edge (m), */
+/* dims[3] voxels, voxel (x, y, z) at index (z * ny + y) * nx + x with centre */
+/* origin + (i + 0.5) * voxel per axis.                                      */
+/* ------------------------------------------------------------------------ */
+
+/* Occupancy: a voxel is occupied when its centre lies in a closed box, or
+ * when its centre is within the UAV's sphere of such a voxel's centre:
+ * dx^2 + dy^2 + dz^2 <= r2 in voxel units (r2 = the inflation radius
+ * squared, in voxels^2, given as an integer). */
+int orc_voxel_occupancy(const double *origin, double voxel, const int32_t *dims,
+                        const double *boxes, int32_t m, int32_t r2, uint8_t *occ)
+{
+    int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    if (nx < 1 || ny < 1 || nz < 1 || m < 0 || r2 < 0 || !(voxel > 0.0))
+        return ORC_ERR_ARG;
+    int64_t nv = nx * ny * nz;
+    uint8_t *core = (uint8_t *)calloc((size_t)nv, 1);
+    if (!core)
+        return ORC_ERR_MEM;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                double c[3] = {origin[0] + ((double)x + 0.5) * voxel,
+                               origin[1] + ((double)y + 0.5) * voxel,
+                               origin[2] + ((double)z + 0.5) * voxel};
+                for (int32_t b = 0; b < m; ++b) {
+                    const double *bx = boxes + 6 * (int64_t)b;
+                    if (c[0] >= bx[0] && c[0] <= bx[3] && c[1] >= bx[1] && c[1] <= bx[4] &&
+                        c[2] >= bx[2] && c[2] <= bx[5]) {
+                        core[(z * ny + y) * nx + x] = 1;
+                        break;
+                    }
+                }
+            }
+    int32_t R = 0;
+    while ((int64_t)(R + 1) * (R + 1) <= r2)
+        ++R;
+    for (int64_t z = 0; z < nz; ++z)
+        for (int64_t y = 0; y < ny; ++y)
+            for (int64_t x = 0; x < nx; ++x) {
+                int o = 0;
+                for (int32_t dz = -R; dz <= R && !o; ++dz)
+                    for (int32_t dy = -R; dy <= R && !o; ++dy)
+                        for (int32_t dx = -R; dx <= R && !o; ++dx) {
+                            if (dx * dx + dy * dy + dz * dz > r2)
+                                continue;
+                            int64_t xx = x + dx, yy = y + dy, zz = z + dz;
+                            if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz)
+                                continue;
+                            o = core[(zz * ny + yy) * nx + xx];
+                        }
+                occ[(z * ny + y) * nx + x] = (uint8_t)o;
+            }
+    free(core);
+    return 0;
+}
+
+/* Open-list entry; the list pops the smallest (f, h, voxel).  Equal keys only
+ * arise for repeated entries of one voxel, so the expansion order is the
+ * same for any correct priority queue. */
+typedef struct {
+    int64_t f, h;
+    int64_t v;
+    int64_t g;
+} orc_open;
+
+static int open_less(const orc_open *a, const orc_open *b)
+{
+    if (a->f != b->f)
+        return a->f < b->f;
+    if (a->h != b->h)
+        return a->h < b->h;
+    return a->v < b->v;
+}
+
+typedef struct {
+    orc_open *heap;
+    int64_t len, cap;
+    int64_t *best; /* best g per voxel, valid where stamp == cur */
+    int32_t *stamp, *closed, cur;
+} orc_astar_ws;
+
+static void heap_push(orc_astar_ws *w, orc_open e)
+{
+    if (w->len == w->cap) {
+        w->cap = w->cap ? 2 * w->cap : 1024;
+        w->heap = (orc_open *)realloc(w->heap, sizeof(orc_open) * (size_t)w->cap);
+    }
+    int64_t i = w->len++;
+    while (i > 0) {
+        int64_t parent = (i - 1) / 2;
+        if (!open_less(&e, &w->heap[parent]))
+            break;
+        w->heap[i] = w->heap[parent];
+        i = parent;
+    }
+    w->heap[i] = e;
+}
+
+static orc_open heap_pop(orc_astar_ws *w)
+{
+    orc_open top = w->heap[0], last = w->heap[--w->len];
+    int64_t i = 0;
+    for (;;) {
+        int64_t c = 2 * i + 1;
+        if (c >= w->len)
+            break;
+        if (c + 1 < w->len && open_less(&w->heap[c + 1], &w->heap[c]))
+            ++c;
+        if (!open_less(&w->heap[c], &last))
+            break;
+        w->heap[i] = w->heap[c];
+        i = c;
+    }
+    if (w->len > 0)
+        w->heap[i] = last;
+    return top;
+}
+
+/* A* from voxel s to voxel t over free voxels, 26 neighbours, step cost
+ * a[0] dx^2 + a[1] dy^2 + a[2] dz^2, heuristic the squared voxel distance to
+ * t, closed voxels never reopened.  Returns the cost g of t, or -1 when t is
+ * not reached before max_exp voxels other than t have been closed. */
+static int64_t astar_one(const uint8_t *occ, const int32_t *dims, int64_t s, int64_t t,
+                         const int32_t *a, int32_t max_exp, orc_astar_ws *w)
+{
+    int64_t nx = dims[0], ny = dims[1], nz = dims[2];
+    int64_t tx = t % nx, ty = (t / nx) % ny, tz = t / (nx * ny);
+    ++w->cur;
+    w->len = 0;
+    int64_t sx = s % nx, sy = (s / nx) % ny, sz = s / (nx * ny);
+    int64_t h0 = (sx - tx) * (sx - tx) + (sy - ty) * (sy - ty) + (sz - tz) * (sz - tz);
+    w->stamp[s] = w->cur;
+    w->best[s] = 0;
+    orc_open e0 = {h0, h0, s, 0};
+    heap_push(w, e0);
+    int64_t expanded = 0;
+    while (w->len > 0) {
+        orc_open e = heap_pop(w);
+        if (w->closed[e.v] == w->cur)
+            continue;
+        w->closed[e.v] = w->cur;
+        if (e.v == t)
+            return e.g;
+        if (expanded >= max_exp)
+            return -1;
+        ++expanded;
+        int64_t x = e.v % nx, y = (e.v / nx) % ny, z = e.v / (nx * ny);
+        for (int dz = -1; dz <= 1; ++dz)
+            for (int dy = -1; dy <= 1; ++dy)
+                for (int dx = -1; dx <= 1; ++dx) {
+                    if (!dx && !dy && !dz)
+                        continue;
+                    int64_t xx = x + dx, yy = y + dy, zz = z + dz;
+                    if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz)
+                        continue;
+                    int64_t v = (zz * ny + yy) * nx + xx;
+                    if (occ[v] || w->closed[v] == w->cur)
+                        continue;
+                    int64_t g = e.g + (int64_t)a[0] * dx * dx + (int64_t)a[1] * dy * dy +
+                                (int64_t)a[2] * dz * dz;
+                    if (w->stamp[v] == w->cur && g >= w->best[v])
+                        continue;
+                    w->stamp[v] = w->cur;
+                    w->best[v] = g;
+                    int64_t h = (xx - tx) * (xx - tx) + (yy - ty) * (yy - ty) + (zz - tz) * (zz - tz);
+                    orc_open ne = {g + h, h, v, g};
+                    heap_push(w, ne);
+                }
+    }
+    return -1;
+}
+
+/* C[i][j] = unit_mm * (A* cost from the voxel of viewpoint i to that of j),
+ * i < j, mirrored, zero diagonal; blocked_cost where a viewpoint lies outside
+ * the grid or in an occupied voxel, or no path was found within max_exp
+ * expansions.  The voxel of a point is floor((p - origin) / voxel) per axis.
+ * Returns ORC_ERR_RANGE (entries clamped) when an entry exceeds 2^29. */
+int orc_cost_matrix_astar(const double *xyz, int32_t n, const uint8_t *occ,
+                          const double *origin, double voxel, const int32_t *dims,
+                          const int32_t *a, int32_t unit_mm, int32_t blocked_cost,
+                          int32_t max_exp, int32_t *C)
+{
+    if (n < 1 || unit_mm < 0 || blocked_cost < 0 || max_exp < 0 || a[0] < 0 || a[1] < 0 ||
+        a[2] < 0 || !(voxel > 0.0))
+        return ORC_ERR_ARG;
+    int64_t nx = dims[0], ny = dims[1], nz = dims[2], nv = nx * ny * nz;
+    int64_t *vox = (int64_t *)malloc(sizeof(int64_t) * (size_t)n);
+    orc_astar_ws w = {0};
+    w.best = (int64_t *)malloc(sizeof(int64_t) * (size_t)nv);
+    w.stamp = (int32_t *)calloc((size_t)nv, sizeof(int32_t));
+    w.closed = (int32_t *)calloc((size_t)nv, sizeof(int32_t));
+    for (int32_t i = 0; i < n; ++i) {
+        int64_t c[3];
+        int inside = 1;
+        for (int k = 0; k < 3; ++k) {
+            c[k] = (int64_t)floor((xyz[3 * (int64_t)i + k] - origin[k]) / voxel);
+            inside &= c[k] >= 0 && c[k] < dims[k];
+        }
+        vox[i] = inside ? (c[2] * ny + c[1]) * nx + c[0] : -1;
+        if (vox[i] >= 0 && occ[vox[i]])
+            vox[i] = -1;
+    }
+    int status = 0;
+    for (int32_t i = 0; i < n; ++i) {
+        C[(int64_t)i * n + i] = 0;
+        for (int32_t j = i + 1; j < n; ++j) {
+            int64_t g = (vox[i] < 0 || vox[j] < 0) ? -1 : astar_one(occ, dims, vox[i], vox[j], a,
+                                                                    max_exp, &w);
+            int64_t v = g < 0 ? (int64_t)blocked_cost : g * unit_mm;
+            if (v > ORC_COST_MAX) {
+                status = ORC_ERR_RANGE;
+                v = ORC_COST_MAX;
+            }
+            C[(int64_t)i * n + j] = (int32_t)v;
+            C[(int64_t)j * n + i] = (int32_t)v;
+        }
+    }
+    free(vox);
+    free(w.heap);
+    free(w.best);
+    free(w.stamp);
+    free(w.closed);
+    return status;
+}
+
 /* Eq. (min) for the tour x (closing edge included). */
 int64_t orc_fitness(const int32_t *C, int32_t n, const uint16_t *x)
 {

@@ -635,3 +635,131 @@ def test_inertia_truncates_canonical_velocity(oracle_mod, w):
         assert sw.vel_len(p) == keep + ka + kb
         v2 = np.concatenate([canon[:keep], a[:ka], b[:kb]])
         assert np.array_equal(s2["X"][p], oracle_mod.apply(s1["X"][p], v2))
+
+
+# ------------------------------------------------------------ A* edge costs
+
+def _grid_graph(occ, weights):
+    """Sparse 26-neighbour graph of the free voxels (for scipy's Dijkstra)."""
+    from scipy.sparse import coo_matrix
+    nz, ny, nx = occ.shape
+    rows, cols, vals = [], [], []
+    idx = np.arange(nx * ny * nz).reshape(nz, ny, nx)
+    for dz in (-1, 0, 1):
+        for dy in (-1, 0, 1):
+            for dx in (-1, 0, 1):
+                if not (dx or dy or dz):
+                    continue
+                zs = slice(max(0, -dz), nz - max(0, dz))
+                ys = slice(max(0, -dy), ny - max(0, dy))
+                xs = slice(max(0, -dx), nx - max(0, dx))
+                zt = slice(max(0, dz), nz - max(0, -dz))
+                yt = slice(max(0, dy), ny - max(0, -dy))
+                xt = slice(max(0, dx), nx - max(0, -dx))
+                ok = (occ[zs, ys, xs] == 0) & (occ[zt, yt, xt] == 0)
+                rows.append(idx[zs, ys, xs][ok])
+                cols.append(idx[zt, yt, xt][ok])
+                w = weights[0] * dx * dx + weights[1] * dy * dy + weights[2] * dz * dz
+                vals.append(np.full(int(ok.sum()), w, np.float64))
+    n = nx * ny * nz
+    return coo_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(n, n)).tocsr()
+
+
+def test_voxel_occupancy_hand_case(oracle_mod):
+    """Two voxel centres in a closed box (one face touching), then the
+    6-neighbour shell for an inflation radius of one voxel."""
+    dims = (6, 5, 3)
+    box = [(1.2, 1.0, 0.5, 2.8, 1.9, 0.5)]  # centres (1.5|2.5, 1.5, 0.5): z on the face
+    occ = oracle_mod.voxel_occupancy((0, 0, 0), 1.0, dims, box, 0)
+    core = {(1, 1, 0), (2, 1, 0)}
+    assert {tuple(v[::-1]) for v in np.argwhere(occ)} == core
+    occ1 = oracle_mod.voxel_occupancy((0, 0, 0), 1.0, dims, box, 1)
+    shell = {(0, 1, 0), (1, 0, 0), (1, 2, 0), (1, 1, 1), (3, 1, 0), (2, 0, 0), (2, 2, 0), (2, 1, 1)}
+    assert {tuple(v[::-1]) for v in np.argwhere(occ1)} == core | shell
+
+
+def test_astar_single_axis_corridors_pin_the_weights(oracle_mod):
+    """In a one-voxel-wide corridor along an axis the only path is straight:
+    cost = that axis' weight x the voxel count (pins the weight of each axis)."""
+    weights = (2, 3, 5)
+    for axis in range(3):
+        dims = [1, 1, 1]
+        dims[axis] = 9
+        xyz = np.zeros((2, 3))
+        xyz[0, axis], xyz[1, axis] = 0.5, 7.5
+        occ = np.zeros(dims[::-1], np.uint8)
+        C, st = oracle_mod.cost_matrix_astar(xyz, occ, (0, 0, 0), 1.0, dims, weights, unit_mm=1)
+        assert st == 0 and C[0, 1] == C[1, 0] == 7 * weights[axis]
+
+
+def test_astar_empty_grid_unit_weights_is_manhattan(oracle_mod):
+    """Unit weights on an empty grid: every step moving toward the goal costs
+    the number of axes it moves, so the cost is the Manhattan distance."""
+    dims = (9, 8, 7)
+    rng = np.random.default_rng(3)
+    pts = rng.integers(0, dims, size=(12, 3)) + 0.5
+    occ = np.zeros(dims[::-1], np.uint8)
+    C, st = oracle_mod.cost_matrix_astar(pts, occ, (0, 0, 0), 1.0, dims, (1, 1, 1), unit_mm=1)
+    man = np.abs(pts[:, None, :] - pts[None, :, :]).sum(axis=2)
+    assert st == 0 and np.array_equal(C, man.astype(np.int32))
+
+
+@pytest.mark.parametrize("weights", [(1, 1, 1), (1, 2, 3)])
+def test_astar_cost_is_at_least_the_shortest_path(oracle_mod, weights):
+    """The heuristic is the squared distance (not admissible), so A* may miss
+    the shortest path but never beats it: compare with scipy's Dijkstra on
+    the same voxel graph; unreachable goals get the blocked cost."""
+    from scipy.sparse.csgraph import dijkstra
+    dims = (10, 9, 4)
+    rng = np.random.default_rng(sum(weights))
+    boxes = []
+    for _ in range(6):
+        lo = rng.uniform(0, (10, 9, 4))
+        boxes.append(tuple(lo) + tuple(lo + rng.uniform(0.5, 3.0, 3)))
+    occ = oracle_mod.voxel_occupancy((0, 0, 0), 1.0, dims, boxes, 0)
+    free = np.argwhere(occ == 0)
+    pick = free[rng.choice(len(free), 14, replace=False)]
+    pts = pick[:, ::-1] + 0.5
+    C, st = oracle_mod.cost_matrix_astar(pts, occ, (0, 0, 0), 1.0, dims, weights, unit_mm=1,
+                                         blocked_cost=10 ** 6)
+    G = _grid_graph(occ, weights)
+    src = [(int(z) * 9 + int(y)) * 10 + int(x) for z, y, x in pick]
+    D = dijkstra(G, indices=src)[:, src]
+    for i in range(len(src)):
+        for j in range(i + 1, len(src)):
+            if np.isinf(D[i, j]):
+                assert C[i, j] == 10 ** 6
+            else:
+                assert C[i, j] >= D[i, j]
+
+
+def test_astar_blocked_cases(oracle_mod):
+    dims = (7, 7, 3)
+    # the goal voxel (3, 3, 1) is walled in on all 26 sides
+    boxes = [(2.0, 2.0, 0.0, 5.0, 5.0, 3.0)]
+    occ = oracle_mod.voxel_occupancy((0, 0, 0), 1.0, dims, boxes, 0)
+    occ[1, 3, 3] = 0
+    pts = np.array([[0.5, 0.5, 0.5], [3.5, 3.5, 1.5], [6.5, 6.5, 2.5], [9.0, 1.0, 1.0]])
+    C, st = oracle_mod.cost_matrix_astar(pts, occ, (0, 0, 0), 1.0, dims, unit_mm=1,
+                                         blocked_cost=777)
+    assert C[0, 1] == C[1, 2] == 777          # enclosed goal
+    assert C[0, 3] == C[3, 2] == 777          # outside the grid
+    assert C[0, 2] not in (0, 777)
+    # an expansion cap of zero reaches only the start voxel itself
+    C0, _ = oracle_mod.cost_matrix_astar(pts[[0, 0, 2]], occ, (0, 0, 0), 1.0, dims, unit_mm=1,
+                                         blocked_cost=777, max_expansions=0)
+    assert C0[0, 1] == 0 and C0[0, 2] == 777
+
+
+def test_astar_squared_heuristic_trap(oracle_mod):
+    """The squared heuristic is not admissible: on a 5 x 4 grid with one
+    obstacle at (1, 2), from (3, 3) to (0, 2) the shortest path costs 4 (two
+    face steps and a diagonal), but the search, traced by hand, pops (2, 2)
+    (f = 2 + 4), then (1, 1) (f = 4 + 2, before (1, 3) by index), from which
+    the goal enters the open list at g = 6 with h = 0 and is popped first."""
+    occ = np.zeros((1, 4, 5), np.uint8)
+    occ[0, 2, 1] = 1
+    pts = np.array([[3.5, 3.5, 0.5], [0.5, 2.5, 0.5]])
+    C, st = oracle_mod.cost_matrix_astar(pts, occ, (0, 0, 0), 1.0, (5, 4, 1), unit_mm=1)
+    assert st == 0 and C[0, 1] == 6

@@ -55,6 +55,8 @@ def workload(name: str):
         return inputs.batched()[0]
     if name == "serving":      # ... or the first request of the stream
         return inputs.serving(count=1)[0][1]
+    if name == "astar":        # ... or the facade's swarm
+        return inputs.facade()
     return inputs.CONFIGS[name]()
 
 
@@ -571,6 +573,75 @@ def serving_line(args):
     }
 
 
+def astar_line(args):
+    """A* edge costs (Sec. 2.2) for every viewpoint pair of the facade or
+    bridge workload on a 0.5 m voxel grid with its boxes inflated by a 0.5 m
+    UAV: occupancy plus the full matrix per step."""
+    import numpy as np
+    import torch
+
+    from paper_1706_04399_gb300 import dpso, inputs
+
+    torch.cuda.set_device(0)
+    inst = inputs.CONFIGS[args.astar_instance]()
+    voxel = 0.5
+    origin, dims = inputs.voxel_grid(inst, voxel)
+    ap = dpso.astar_params(origin, voxel, dims, inflate_r2=inputs.inflate_r2(0.5, voxel),
+                           unit_mm=int(round(1000 * voxel)))
+    n = inst.n
+    npairs = n * (n - 1) // 2
+    stream = torch.cuda.current_stream()
+    xyz = torch.from_numpy(inst.xyz).cuda()
+    boxes = torch.from_numpy(inst.boxes).cuda()
+    occ = torch.empty(int(np.prod(dims)), dtype=torch.uint8, device="cuda")
+    C = torch.empty((n, n), dtype=torch.int32, device="cuda")
+
+    def step():
+        dpso.dpso_voxel_occupancy(boxes, inst.m, ap, occ, stream)
+        dpso.dpso_cost_matrix_astar(xyz, n, occ, ap, C, stream)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    sampler = ClockSampler(gpu_index_for_smi(0))
+    with sampler:
+        for k in range(args.steps):
+            evs[k][0].record(stream)
+            step()
+            evs[k][1].record(stream)
+        torch.cuda.synchronize()
+    ms = sum(a.elapsed_time(b) for a, b in evs) / args.steps
+    Cn = C.cpu().numpy()
+    blocked = int((Cn == ap.blocked_cost).sum() // 2)
+    cpu = None
+    if not args.no_cpu_baseline:
+        import oracle
+        k = min(n, 400)  # the whole facade matrix; the first 400 viewpoints of the bridge
+        occ_ref = oracle.voxel_occupancy(origin, voxel, dims, inst.boxes, ap.inflate_r2)
+        t0 = time.perf_counter()
+        Cref, _ = oracle.cost_matrix_astar(inst.xyz[:k], occ_ref, origin, voxel, dims,
+                                           unit_mm=ap.unit_mm, blocked_cost=ap.blocked_cost,
+                                           max_expansions=ap.max_expansions)
+        csec = time.perf_counter() - t0
+        cpu = {"value": k * (k - 1) / 2 / csec, "unit": "viewpoint-pairs/s", "cores": 1,
+               "kind": "oracle", "sample": f"A* matrix of the first {k} viewpoints ({csec:.2f} s)",
+               "matches_gpu": bool(np.array_equal(Cref, Cn[:k, :k])), "cpu": cpu_model()}
+    return {
+        "metric": METRIC, "value": npairs / (ms / 1e3), "unit": "viewpoint-pairs/s", "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "i32/f64", "data": "synthetic",
+        "config": {"workload": f"astar-{inst.name}-{n}vp", "n": n, "voxel_m": voxel,
+                   "grid": [int(v) for v in dims], "inflate_r2": ap.inflate_r2,
+                   "weights": list(ap.weights), "max_expansions": ap.max_expansions,
+                   "blocked_pairs": blocked,
+                   "l2": "inputs rebuilt every step (occupancy and matrix)"},
+        "gpu_launches": None, "roofline": None, "cpu_baseline": cpu, "e2e": None,
+        "clocks": sampler.summary(),
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -578,7 +649,9 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="facade",
-                    choices=["tiny", "facade", "bridge", "batched", "serving"])
+                    choices=["tiny", "facade", "bridge", "batched", "serving", "astar"])
+    ap.add_argument("--astar-instance", default="facade", choices=["facade", "bridge"],
+                    help="astar: whose viewpoints and boxes")
     ap.add_argument("--instances", type=int, default=256, help="batched: instances")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests")
     ap.add_argument("--max-n", type=int, default=400, help="serving: largest request taken")
@@ -598,6 +671,8 @@ def main(argv=None):
         out = batched_line(args)
     elif args.workload == "serving":
         out = serving_line(args)
+    elif args.workload == "astar":
+        out = astar_line(args)
     else:
         out = gpu_line(args)
     if out is not None:

@@ -189,6 +189,54 @@ int dpso_two_opt_noalloc(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, i
                          int64_t *moves_host, void *stream);
 
 /*
+ * Edge costs by A* over a voxel grid (Sec. 2.2, Eqs. (L) and (cost)), the
+ * paper's alternative to straight segments.  The grid is given: `origin`
+ * (m), `voxel_m` (edge, m), `dims` (nx, ny, nz; each <= 4096); voxel (x, y, z)
+ * has index (z ny + y) nx + x and centre origin + (i + 0.5) voxel_m per axis.
+ * A voxel is occupied when its centre lies in a closed box or within the
+ * UAV's sphere of such a voxel's centre: dx^2 + dy^2 + dz^2 <= inflate_r2
+ * (voxels^2, <= 1024).  A* runs between the voxels of viewpoints i < j
+ * (floor((p - origin) / voxel_m) per axis) over free voxels: 26 neighbours,
+ * step cost weights[0] dx^2 + weights[1] dy^2 + weights[2] dz^2 (<= 1000
+ * each), heuristic the squared voxel distance to the goal, closed voxels never
+ * reopened, ties to the smallest (f, h, voxel).  C[i][j] = C[j][i] =
+ * unit_mm x the path cost; blocked_cost when a viewpoint lies outside the grid
+ * or in an occupied voxel, or when max_expansions voxels were closed without
+ * reaching the goal.
+ */
+#define DPSO_ASTAR_MAX_EXPANSIONS 100000
+typedef struct {
+    double origin[3];
+    double voxel_m;
+    int32_t dims[3];
+    int32_t inflate_r2;
+    int32_t weights[3];
+    int32_t unit_mm;
+    int32_t blocked_cost;
+    int32_t max_expansions; /* <= DPSO_ASTAR_MAX_EXPANSIONS */
+    int32_t reserved;       /* must be 0 */
+} dpso_astar_params;
+
+/* voxel_m 0.5, dims 1 x 1 x 1, weights 1, unit_mm 500, blocked_cost 1e8,
+ * max_expansions 20000, no inflation, origin 0. */
+void dpso_default_astar_params(dpso_astar_params *p);
+
+/* Occupancy (uint8, nx ny nz, 1 = occupied) of the grid for m boxes (device,
+ * m x 6 lo/hi).  Synchronises `stream`.  Errors: DPSO_ERR_ARG, DPSO_ERR_RANGE
+ * (grid or inflation above the limits), DPSO_ERR_NO_MEMORY. */
+int dpso_voxel_occupancy(const double *boxes_dev, int32_t m, const dpso_astar_params *ap,
+                         uint8_t *occ_dev, void *stream);
+
+/* n x n int32 A* cost matrix (device, row-major) for n viewpoints (device,
+ * n x 3) over the occupancy `occ_dev`.  One thread per pair; each search
+ * first gets room for 256 expansions, and pairs that need more are searched
+ * again with room for max_expansions.  Synchronises `stream`.  Errors:
+ * DPSO_ERR_ARG, DPSO_ERR_RANGE (also: an entry above DPSO_COST_MAX, clamped),
+ * DPSO_ERR_NO_MEMORY. */
+int dpso_cost_matrix_astar(const double *xyz_dev, int32_t n, const uint8_t *occ_dev,
+                           const dpso_astar_params *ap, int32_t *C_dev, void *stream);
+
+/*
  * Node-swap exchange (the "swap nodes(i,j) and evaluate fitness" reading of
  * the edge exchange in the paper's GPU listing, Sec. 3.2.3): for each of the
  * `count` tours, repeatedly swap the two positions i < j (every pair of the

@@ -34,6 +34,7 @@ SOURCES = {
     "two_opt_noalloc.cu": [],
     "probe.cu": [],
     "server.cu": [],
+    "astar.cu": ["-fmad=false"],
 }
 
 

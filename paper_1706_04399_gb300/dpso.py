@@ -77,6 +77,14 @@ SERVE_ARRIVAL_ORDER = 0
 SERVE_SHORTEST_FIRST = 1
 
 
+class dpso_astar_params(ctypes.Structure):
+    _fields_ = [("origin", ctypes.c_double * 3), ("voxel_m", ctypes.c_double),
+                ("dims", ctypes.c_int32 * 3), ("inflate_r2", ctypes.c_int32),
+                ("weights", ctypes.c_int32 * 3), ("unit_mm", ctypes.c_int32),
+                ("blocked_cost", ctypes.c_int32), ("max_expansions", ctypes.c_int32),
+                ("reserved", ctypes.c_int32)]
+
+
 class dpso_server_params(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_int32),
                 ("generations_per_tick", ctypes.c_int32), ("policy", ctypes.c_int32),
@@ -125,6 +133,12 @@ def lib():
                                                 ctypes.POINTER(dpso_cost_params), _vp, _vp]),
             "dpso_fitness": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
             "dpso_two_opt": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p, _vp]),
+            "dpso_default_astar_params": (None, [ctypes.POINTER(dpso_astar_params)]),
+            "dpso_voxel_occupancy": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(dpso_astar_params),
+                                                    _vp, _vp]),
+            "dpso_cost_matrix_astar": (ctypes.c_int, [_vp, _i32, _vp,
+                                                      ctypes.POINTER(dpso_astar_params), _vp,
+                                                      _vp]),
             "dpso_node_swap": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p, _vp]),
             "dpso_two_opt_noalloc": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p,
                                                     _vp]),
@@ -247,6 +261,33 @@ def dpso_node_swap(C_dev, n: int, tours_dev, count: int, cost_dev, max_moves: in
                                 ctypes.byref(pairs), ctypes.byref(moves), _stream(stream)),
            "dpso_node_swap")
     return pairs.value, moves.value
+
+
+def astar_params(origin, voxel_m: float, dims, inflate_r2: int = 0, weights=(1, 1, 1),
+                 unit_mm: int = 500, blocked_cost: int = 100_000_000,
+                 max_expansions: int = 20000) -> dpso_astar_params:
+    p = dpso_astar_params()
+    lib().dpso_default_astar_params(ctypes.byref(p))
+    p.origin[:] = [float(v) for v in origin]
+    p.voxel_m = voxel_m
+    p.dims[:] = [int(v) for v in dims]
+    p.inflate_r2 = inflate_r2
+    p.weights[:] = [int(v) for v in weights]
+    p.unit_mm = unit_mm
+    p.blocked_cost = blocked_cost
+    p.max_expansions = max_expansions
+    return p
+
+
+def dpso_voxel_occupancy(boxes_dev, m: int, ap: dpso_astar_params, occ_dev, stream=None) -> None:
+    _check(lib().dpso_voxel_occupancy(_dev(boxes_dev), m, ctypes.byref(ap), _dev(occ_dev),
+                                      _stream(stream)), "dpso_voxel_occupancy")
+
+
+def dpso_cost_matrix_astar(xyz_dev, n: int, occ_dev, ap: dpso_astar_params, C_dev,
+                           stream=None) -> None:
+    _check(lib().dpso_cost_matrix_astar(_dev(xyz_dev), n, _dev(occ_dev), ctypes.byref(ap),
+                                        _dev(C_dev), _stream(stream)), "dpso_cost_matrix_astar")
 
 
 def dpso_probe_l2_read_gbs(nbytes: int = 24 << 20, reps: int = 40, stream=None) -> float:

@@ -214,4 +214,22 @@ def random_cost_matrix(n: int, gen_seed: int, hi: int = 100000) -> np.ndarray:
     return np.ascontiguousarray(c.astype(np.int32))
 
 
+def voxel_grid(inst: Instance, voxel_m: float, margin: int = 2):
+    """A voxel grid spec covering the viewpoints and boxes with `margin` voxels
+    to spare: (origin (3,), dims (3,)) with the origin on multiples of voxel_m."""
+    pts = [inst.xyz]
+    if inst.m:
+        pts += [inst.boxes[:, :3], inst.boxes[:, 3:]]
+    allp = np.concatenate(pts)
+    lo = np.floor(allp.min(axis=0) / voxel_m) * voxel_m - margin * voxel_m
+    hi = allp.max(axis=0) + margin * voxel_m
+    dims = np.ceil((hi - lo) / voxel_m).astype(np.int32) + 1
+    return lo.astype(np.float64), dims
+
+
+def inflate_r2(radius_m: float, voxel_m: float) -> int:
+    """The UAV sphere as an integer squared radius in voxel units."""
+    return int(math.floor((radius_m / voxel_m) ** 2 + 1e-9))
+
+
 CONFIGS = {"tiny": tiny, "facade": facade, "bridge": bridge}

@@ -13,8 +13,12 @@
 //    goal, a closed list (no reopening) and lazy open-list entries popped by
 //    the smallest (f, h, voxel); with that total order the expansion order,
 //    hence the cost, does not depend on how the priority queue is built.
+//  * Pairs whose voxels lie in different connected components of the free
+//    voxels (union-find over the 26-neighbourhood) are blocked without a
+//    search: A* could only exhaust its open list or its cap there.
 //  * Each search has its own binary heap and open-addressing map (voxel ->
-//    best g, closed) in device scratch.  Pass 1 gives every pair room for 256
+//    best g, closed; slots stamped by search, so nothing is cleared) in
+//    device scratch.  Pass 1 gives every pair room for 256
 //    expansions; pairs that need more are searched again, from the start,
 //    with room for the full expansion cap.
 //  * C[i][j] = C[j][i] = g * unit_mm; blocked_cost where a viewpoint lies
@@ -111,9 +115,12 @@ __device__ __forceinline__ bool open_less(const OpenEntry& a, const OpenEntry& b
     return a.v < b.v;
 }
 
-struct MapSlot {  // voxel -> best g and closed flag; v == -1: empty
+// Voxel -> best g and closed flag.  A slot belongs to the search whose stamp
+// it carries (tag >> 1; the scratch starts zeroed and stamps start at 1), so
+// no search has to clear the map of the previous one.
+struct MapSlot {
     int v;
-    int closed;
+    unsigned tag;  // (stamp << 1) | closed
     long long g;
 };
 
@@ -121,7 +128,9 @@ struct AstarArgs {
     AstarGrid gr;
     const unsigned char* occ;
     const int* vox;
+    const int* comp;     // connected component (smallest voxel index) of free voxels
     const int2* pairs;   // (i, j), i < j
+    int stamp0;          // stamp of pairs[0] (stamps are unique within a pass)
     int npairs;
     int a1, a2, a3;
     long long unit_mm;
@@ -142,17 +151,18 @@ __device__ __forceinline__ unsigned slot_of(int v, int bits) {
     return (static_cast<unsigned>(v) * 2654435761u) >> (32 - bits);
 }
 
-// Finds (insert = false) or inserts the slot of voxel v.
-__device__ MapSlot* map_find(MapSlot* map, int bits, int v, bool insert) {
+// Finds (insert = false) or inserts the slot of voxel v for this search.
+__device__ MapSlot* map_find(MapSlot* map, int bits, unsigned stamp, int v, bool insert) {
     const unsigned mask = (1u << bits) - 1u;
     unsigned s = slot_of(v, bits);
     for (unsigned probe = 0; probe <= mask; ++probe, s = (s + 1) & mask) {
         MapSlot* e = map + s;
-        if (e->v == v) return e;
-        if (e->v == -1) {
+        const bool mine = (e->tag >> 1) == stamp;
+        if (mine && e->v == v) return e;
+        if (!mine) {
             if (!insert) return nullptr;
             e->v = v;
-            e->closed = 0;
+            e->tag = stamp << 1;
             e->g = LLONG_MAX;
             return e;
         }
@@ -167,11 +177,12 @@ __global__ void astar_pairs_kernel(AstarArgs A) {
     const int s = A.vox[pr.x], t = A.vox[pr.y];
     long long result = -1;  // path cost, or -1: blocked
     bool retry = false;
-    if (s >= 0 && t >= 0) {
+    // different components: no search can reach t (it would exhaust its open
+    // list or its cap), so the pair is blocked without one
+    if (s >= 0 && t >= 0 && A.comp[s] == A.comp[t]) {
         OpenEntry* heap = A.heap + static_cast<size_t>(k) * A.heap_cap;
         MapSlot* map = A.map + (static_cast<size_t>(k) << A.map_bits);
-        const size_t slots = size_t(1) << A.map_bits;
-        for (size_t q = 0; q < slots; ++q) map[q].v = -1;
+        const unsigned stamp = static_cast<unsigned>(A.stamp0 + k);
         const int nx = A.gr.nx, ny = A.gr.ny, nz = A.gr.nz;
         const int tx = t % nx, ty = (t / nx) % ny, tz = t / (nx * ny);
         int len = 0;
@@ -202,16 +213,16 @@ __global__ void astar_pairs_kernel(AstarArgs A) {
         {
             const int sx = s % nx, sy = (s / nx) % ny, sz = s / (nx * ny);
             const int h0 = (sx - tx) * (sx - tx) + (sy - ty) * (sy - ty) + (sz - tz) * (sz - tz);
-            MapSlot* e0 = map_find(map, A.map_bits, s, true);
+            MapSlot* e0 = map_find(map, A.map_bits, stamp, s, true);
             e0->g = 0;
             push(OpenEntry{h0, 0, h0, s});
         }
         int expanded = 0;
         while (len > 0) {
             const OpenEntry e = pop();
-            MapSlot* me = map_find(map, A.map_bits, e.v, false);
-            if (me->closed) continue;
-            me->closed = 1;
+            MapSlot* me = map_find(map, A.map_bits, stamp, e.v, false);
+            if (me->tag & 1u) continue;
+            me->tag |= 1u;
             if (e.v == t) {
                 result = e.g;
                 break;
@@ -230,8 +241,8 @@ __global__ void astar_pairs_kernel(AstarArgs A) {
                         if (xx < 0 || yy < 0 || zz < 0 || xx >= nx || yy >= ny || zz >= nz) continue;
                         const int v = (zz * ny + yy) * nx + xx;
                         if (A.occ[v]) continue;
-                        MapSlot* sl = map_find(map, A.map_bits, v, true);
-                        if (sl->closed) continue;
+                        MapSlot* sl = map_find(map, A.map_bits, stamp, v, true);
+                        if (sl->tag & 1u) continue;
                         const long long g = e.g + static_cast<long long>(A.a1) * dx * dx +
                                             static_cast<long long>(A.a2) * dy * dy +
                                             static_cast<long long>(A.a3) * dz * dz;
@@ -254,6 +265,61 @@ __global__ void astar_pairs_kernel(AstarArgs A) {
     }
     A.C[static_cast<size_t>(pr.x) * A.n + pr.y] = static_cast<int>(c);
     A.C[static_cast<size_t>(pr.y) * A.n + pr.x] = static_cast<int>(c);
+}
+
+// Connected components of the free voxels (26-neighbourhood) by union-find:
+// every root ends at the smallest voxel index of its component whatever the
+// order of the unions (hook the larger root under the smaller by CAS).
+__device__ int cc_find(int* parent, int v) {
+    int p = parent[v];
+    while (p != v) {
+        const int gp = parent[p];
+        if (gp != p) parent[v] = gp;  // halve the path (benign races)
+        v = p;
+        p = gp;
+    }
+    return v;
+}
+
+__global__ void cc_init_kernel(const unsigned char* __restrict__ occ, long long nv, int* parent) {
+    for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < nv;
+         v += static_cast<long long>(gridDim.x) * blockDim.x)
+        parent[v] = occ[v] ? -1 : static_cast<int>(v);
+}
+
+__global__ void cc_union_kernel(AstarGrid gr, const unsigned char* __restrict__ occ, int* parent) {
+    const long long nv = static_cast<long long>(gr.nx) * gr.ny * gr.nz;
+    for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < nv;
+         v += static_cast<long long>(gridDim.x) * blockDim.x) {
+        if (occ[v]) continue;
+        const int x = static_cast<int>(v % gr.nx), y = static_cast<int>((v / gr.nx) % gr.ny),
+                  z = static_cast<int>(v / (static_cast<long long>(gr.nx) * gr.ny));
+        for (int d = 14; d < 27; ++d) {  // the 13 neighbours after v in index order
+            const int dx = d % 3 - 1, dy = (d / 3) % 3 - 1, dz = d / 9 - 1;
+            const int xx = x + dx, yy = y + dy, zz = z + dz;
+            if (xx < 0 || yy < 0 || zz < 0 || xx >= gr.nx || yy >= gr.ny || zz >= gr.nz) continue;
+            const int u = (zz * gr.ny + yy) * gr.nx + xx;
+            if (occ[u]) continue;
+            int a = cc_find(parent, static_cast<int>(v)), b = cc_find(parent, u);
+            while (a != b) {
+                if (a > b) {
+                    const int t = a;
+                    a = b;
+                    b = t;
+                }
+                const int old = atomicCAS(parent + b, b, a);  // hook root b under a
+                if (old == b) break;
+                b = cc_find(parent, old);
+                a = cc_find(parent, a);
+            }
+        }
+    }
+}
+
+__global__ void cc_flatten_kernel(long long nv, int* parent) {
+    for (long long v = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; v < nv;
+         v += static_cast<long long>(gridDim.x) * blockDim.x)
+        if (parent[v] >= 0) parent[v] = cc_find(parent, static_cast<int>(v));
 }
 
 __global__ void zero_diagonal_kernel(int* C, int n) {
@@ -297,6 +363,11 @@ cudaError_t run_pass(AstarArgs A, const int2* pairs, int npairs, size_t budget, 
     MapSlot* map = nullptr;
     cudaError_t e = cudaMallocAsync(&heap, per * chunk, st);
     if (e != cudaSuccess) return e;
+    e = cudaMemsetAsync(heap, 0, per * chunk, st);  // map tags 0: no search owns a slot
+    if (e != cudaSuccess) {
+        cudaFreeAsync(heap, st);
+        return e;
+    }
     map = reinterpret_cast<MapSlot*>(reinterpret_cast<char*>(heap) +
                                      static_cast<size_t>(A.heap_cap) * sizeof(OpenEntry) * chunk);
     A.heap = heap;
@@ -305,6 +376,7 @@ cudaError_t run_pass(AstarArgs A, const int2* pairs, int npairs, size_t budget, 
     for (int first = 0; first < npairs && e == cudaSuccess; first += chunk) {
         A.pairs = pairs + first;
         A.npairs = std::min(chunk, npairs - first);
+        A.stamp0 = first + 1;
         A.retry = retry_base ? retry_base + first : nullptr;
         astar_pairs_kernel<<<(A.npairs + 127) / 128, 128, 0, st>>>(A);
         e = cudaGetLastError();
@@ -370,9 +442,11 @@ int dpso_cost_matrix_astar(const double* xyz_dev, int32_t n, const uint8_t* occ_
     pairs.reserve(static_cast<size_t>(np));
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) pairs.push_back(make_int2(i, j));
-    int *vox = nullptr, *retry = nullptr, *err = nullptr;
+    int *vox = nullptr, *retry = nullptr, *err = nullptr, *comp = nullptr;
     int2* dpairs = nullptr;
+    const long long nv = static_cast<long long>(ap->dims[0]) * ap->dims[1] * ap->dims[2];
     auto cleanup = [&](int code) {
+        cudaFreeAsync(comp, s);
         cudaFreeAsync(vox, s);
         cudaFreeAsync(retry, s);
         cudaFreeAsync(err, s);
@@ -383,6 +457,7 @@ int dpso_cost_matrix_astar(const double* xyz_dev, int32_t n, const uint8_t* occ_
     if (cudaMallocAsync(&vox, sizeof(int) * n, s) != cudaSuccess ||
         cudaMallocAsync(&retry, sizeof(int) * std::max<long long>(np, 1), s) != cudaSuccess ||
         cudaMallocAsync(&err, sizeof(int), s) != cudaSuccess ||
+        cudaMallocAsync(&comp, sizeof(int) * nv, s) != cudaSuccess ||
         cudaMallocAsync(&dpairs, sizeof(int2) * std::max<long long>(np, 1), s) != cudaSuccess) {
         cudaGetLastError();
         return cleanup(DPSO_ERR_NO_MEMORY);
@@ -400,10 +475,18 @@ int dpso_cost_matrix_astar(const double* xyz_dev, int32_t n, const uint8_t* occ_
         zero_diagonal_kernel<<<(n + 127) / 128, 128, 0, s>>>(C_dev, n);
         e = cudaGetLastError();
     }
+    if (e == cudaSuccess) {  // components of the free voxels
+        const int blocks = static_cast<int>(std::min<long long>((nv + 255) / 256, 65536));
+        cc_init_kernel<<<blocks, 256, 0, s>>>(occ_dev, nv, comp);
+        cc_union_kernel<<<blocks, 256, 0, s>>>(gr, occ_dev, comp);
+        cc_flatten_kernel<<<blocks, 256, 0, s>>>(nv, comp);
+        e = cudaGetLastError();
+    }
     AstarArgs A{};
     A.gr = gr;
     A.occ = occ_dev;
     A.vox = vox;
+    A.comp = comp;
     A.a1 = ap->weights[0];
     A.a2 = ap->weights[1];
     A.a3 = ap->weights[2];

@@ -426,7 +426,6 @@ def batched_line(args):
     batch = dpso.Batch(together, stream)
     rows, tpc, tg = batch.autotune(stream)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
-    S_total = sum(i.swarm for i in insts)
 
     def run(step_fn, steps):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))

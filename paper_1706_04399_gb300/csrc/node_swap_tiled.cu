@@ -309,8 +309,12 @@ cudaError_t launch_ns(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
 }  // namespace
 
 size_t node_swap_tiled_smem(int n, int rows) {
-    // the 2-opt layout with one more staged row
-    return two_opt_tiled_smem(n, rows + 1, 1);
+    // rows + 2 staged cost rows, the column records (n + 4 int2), the tour
+    // (n + 1 uint16, padded to 8)
+    const size_t staged = static_cast<size_t>(rows + 2) * shifted_ld(n) * sizeof(int);
+    const size_t rec = static_cast<size_t>(n + 4) * sizeof(int2);
+    const size_t xs = static_cast<size_t>((n + 1 + 7) / 8 * 8) * sizeof(uint16_t);
+    return staged + rec + xs;
 }
 
 int node_swap_tiled_rows(int n) {

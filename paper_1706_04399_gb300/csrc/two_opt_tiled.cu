@@ -59,7 +59,9 @@ size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages) {
         static_cast<size_t>(stages) * (rows_per_tile + 1) * shifted_ld(n) * sizeof(int);
     const size_t rec = static_cast<size_t>(n + 4) * sizeof(int2);
     const size_t xs = static_cast<size_t>((n + 1 + 7) / 8 * 8) * sizeof(uint16_t);
-    return rows + rec + xs;
+    // the row cache and, per tile subgroup, two 32-key fold buffers
+    const size_t cache = (static_cast<size_t>((n + 1) & ~1) + 64 * stages) * sizeof(uint64_t);
+    return rows + rec + xs + cache;
 }
 
 namespace {
@@ -181,6 +183,8 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         const int buf_words = kStaged * ldq;
         const int rec2 = TG * buf_words / 2;    // int2 index of record 0 (even)
         const int xs16 = (rec2 + n + 4) * 4;    // uint16 index of x_0
+        // u64 index of the row cache, after the tour (n + 1 uint16, padded)
+        const int rk64 = (xs16 + (n + 1 + 7) / 8 * 8 + 3) / 4;
         const int* __restrict__ C = a.C;
         const int ldc = a.ldc;
         const long long npairs = static_cast<long long>(n) * (n - 3) / 2;
@@ -245,19 +249,60 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         int moves = 0, passes = 0;
         group_sync<TPC>(grp);
 
+        // Row cache: rowkey[i] is the smallest (delta, i, group) of row i over
+        // all its columns, from the last pass that evaluated it.  A move that
+        // reverses positions pa+1..pb changes the pairs of rows pa..pb and,
+        // for rows below pa, only columns pa..pb; rows above pb keep theirs.
+        // tk: per subgroup, two 32-entry buffers (by tile parity) where the
+        // subgroup's warps fold their keys for the rows of a tile.
+        unsigned long long* const rowkey = reinterpret_cast<unsigned long long*>(smi) + rk64;
+        unsigned long long* const tk = rowkey + ((n + 1) & ~1) + half * 64;
+        for (int r = tid; r < TG * 64; r += GT) rowkey[((n + 1) & ~1) + r] = ~0ull;
+        int pa = -1, pb = -1;  // the previous move; pb < 0: evaluate every pair
+        group_sync<TPC>(grp);
+
+        // Warp 0 of a subgroup folds the finished tile at I (parity par) into
+        // the row cache: a full tile replaces the rows' keys, a partial one
+        // (only the changed columns evaluated) takes the smaller.
+        auto combine = [&](int I, bool partial, int par) {
+            const int i = I + lane;
+            if (lane < kRows && i <= n - 3) {
+                const unsigned long long v = tk[par * 32 + lane];
+                rowkey[i] = partial ? min(rowkey[i], v) : v;
+            }
+            tk[par * 32 + lane] = ~0ull;
+        };
+
         for (;;) {
             if (a.max_moves > 0 && moves >= a.max_moves) break;
             if (moves >= guard) {
                 if (tid == 0 && a.status) atomicExch(a.status, DPSO_ERR_INTERNAL);
                 break;
             }
-            unsigned long long key = ~0ull;
-            int ke0 = 0, ke1 = 0;
-            for (int t = half; t < ntiles; t += TG) {
+            const bool first = pb < 0;
+            const int tlast = first ? ntiles - 1 : min(ntiles - 1, pb / kRows);
+            int prevI = -1, par = 0;
+            bool prevPartial = false;
+            for (int t = half; t <= tlast; t += TG) {
                 const int I = t * kRows;
                 half_sync<TPC, TG>(grp, half);  // the previous tile is no longer read
                 if (s_abort[sg]) break;  // read after the barrier: the subgroup agrees
+                if (wsg == 0 && prevI >= 0) combine(prevI, prevPartial, par ^ 1);
                 stage(I);
+                // the tile's mode: rows pa..pb (or the first pass) need every
+                // column; rows below pa only pa..pb, unless a row's cached
+                // minimum sits in a group that touches pa..pb
+                const int i = I + lane;
+                const bool row_ok = lane < kRows && i <= n - 3;
+                bool full = first || (I <= pb && I + kRows - 1 >= pa);
+                if (!full) {
+                    bool need = false;
+                    if (row_ok) {
+                        const int cmc = static_cast<int>(rowkey[i] & 0xffffu);
+                        need = cmc + 3 >= pa && cmc <= pb;
+                    }
+                    full = __any_sync(0xffffffffu, need);  // same rows in every warp
+                }
                 stage_wait();
                 // lanes past the tile height idle on a valid row; byte offsets
                 // of this lane's two rows (row start plus its 0..3 word shift)
@@ -266,16 +311,22 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                 const int p2 = half * buf_words + rb1 * ldq + ((rb1 >> 3) & 3);
                 const char* const r1 = reinterpret_cast<const char*>(smi + p1);
                 const char* const r2 = reinterpret_cast<const char*>(smi + p2);
-                // columns in groups of four, contiguous per warp; the records
-                // past n are padding
+                // columns in groups of four from I+2 (partial tiles: the groups
+                // that hold pa..pb, on the same grid), contiguous per warp; the
+                // records past n are padding
                 const int cbeg = I + 2;
-                const int ngroups = (n - cbeg + 3) >> 2;
+                int cstart = cbeg, cstop = n;
+                if (!full) {
+                    cstart = cbeg + ((max(pa, cbeg) - cbeg) & ~3);
+                    cstop = min(n, pb + 1);
+                }
+                const int ngroups = cstop > cstart ? (cstop - cstart + 3) >> 2 : 0;
                 const int g0 = (ngroups * wsg) / WSG, g1 = (ngroups * (wsg + 1)) / WSG;
                 // first valid column of this lane's row (rows past n-3 have none)
-                const int lim = (lane < kRows && I + lane <= n - 3) ? I + lane + 2 : INT_MAX;
+                const int lim = row_ok ? i + 2 : INT_MAX;
                 int m = INT_MAX, cm = 0;
-                int c = cbeg + 4 * g0;
-                const int cend = cbeg + 4 * g1;
+                int c = cstart + 4 * g0;
+                const int cend = cstart + 4 * g1;
                 int q = g0 < g1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
                 const int4* rp = smi4 + ((rec2 + c) >> 1);   // records c .. c+3
                 auto at = [](const char* row, int off) {
@@ -304,37 +355,22 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                 const int cmask = min(cend, I + kStaged);
                 while (c < cmask) group(true);
                 while (c < cend) group(false);
-                if (m != INT_MAX && lim != INT_MAX) {  // idle lanes own no row
-                    // Against the lane's earlier tiles (other rows) the group
-                    // start orders this candidate exactly; only when it wins is
-                    // its column found in the group, with the two costs there.
-                    const int dl = m + smi2[rec2 + I + lane].y;
-                    if (pack_key(dl, I + lane, cm) < key) {
-                        int qv = smi2[rec2 + cm - 1].x;
-                        int jx = -1, e0 = 0, e1 = 0;
-#pragma unroll
-                        for (int u = 0; u < 4; ++u) {
-                            const int2 r = smi2[rec2 + cm + u];
-                            const int a_ = at(r1, qv), b_ = at(r2, r.x);
-                            const int v = cm + u >= lim ? a_ + b_ + r.y : INT_MAX;
-                            if (jx < 0 && v == m) {
-                                jx = cm + u;
-                                e0 = a_;
-                                e1 = b_;
-                            }
-                            qv = r.x;
-                        }
-                        key = pack_key(dl, I + lane, jx);
-                        ke0 = e0;
-                        ke1 = e1;
-                    }
-                }
+                if (m != INT_MAX && row_ok)
+                    atomicMin(&tk[par * 32 + lane], pack_key(m + smi2[rec2 + i].y, i, cm));
+                prevI = I;
+                prevPartial = !full;
+                par ^= 1;
             }
             ++passes;
-            const unsigned long long kw = warp_min_u64(key);
-            if (lane == 0) s_keyg[warp] = kw;
             group_sync<TPC>(grp);
             if (tour_aborted()) break;  // no move from a pass with a missing tile
+            if (wsg == 0 && prevI >= 0) combine(prevI, prevPartial, par ^ 1);
+            group_sync<TPC>(grp);
+            unsigned long long kl = ~0ull;
+            for (int r = tid; r <= n - 3; r += GT) kl = min(kl, rowkey[r]);
+            const unsigned long long kw = warp_min_u64(kl);
+            if (lane == 0) s_keyg[warp] = kw;
+            group_sync<TPC>(grp);
             if (warp == 0) {
                 unsigned long long kk = lane < WPT ? s_keyg[lane] : ~0ull;
                 kk = warp_min_u64(kk);
@@ -345,14 +381,36 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
             if (best == ~0ull) break;
             const int bd = static_cast<int>(static_cast<uint32_t>(best >> 32) ^ 0x80000000u);
             if (bd >= 0) break;
-            if (key == best) {  // exactly one lane evaluated (i*, j*)
-                s_e0[grp] = ke0;
-                s_e1[grp] = ke1;
+            const int bi = static_cast<int>((best >> 16) & 0xffffu);
+            if (tid == 0) {
+                // the winning group's first column of delta bd, with the two
+                // costs of the new edges, from C
+                const int cmg = static_cast<int>(best & 0xffffu);
+                const int xi = smu[xs16 + bi], xi1 = smu[xs16 + bi + 1];
+                int jx = -1, e0 = 0, e1 = 0;
+                for (int u = 0; u < 4 && jx < 0; ++u) {
+                    const int j = cmg + u;
+                    if (j < bi + 2 || j > n - 1) continue;
+                    const int xj = smu[xs16 + j], xj1 = smu[xs16 + j + 1];
+                    const int a_ = C[static_cast<size_t>(xi) * ldc + xj];
+                    const int b_ = C[static_cast<size_t>(xi1) * ldc + xj1];
+                    if (a_ + b_ + smi2[rec2 + j].y + smi2[rec2 + bi].y == bd) {
+                        jx = j;
+                        e0 = a_;
+                        e1 = b_;
+                    }
+                }
+                s_part[grp] = jx;  // (the work item is no longer needed this tour)
+                s_e0[grp] = e0;
+                s_e1[grp] = e1;
             }
             group_sync<TPC>(grp);
-            const int bi = static_cast<int>((best >> 16) & 0xffffu);
-            const int bj = static_cast<int>(best & 0xffffu);
+            const int bj = s_part[grp];
             const int ei = s_e0[grp], ej = s_e1[grp];
+            if (bj < 0) {  // cannot happen: the cache and C disagree
+                if (tid == 0 && a.status) atomicExch(a.status, DPSO_ERR_INTERNAL);
+                break;
+            }
             // reverse x[bi+1..bj] and the edge terms strictly between bi and bj
             for (int q2 = tid; q2 < (bj - bi) / 2; q2 += GT) {
                 const uint16_t t0 = smu[xs16 + bi + 1 + q2];
@@ -370,6 +428,8 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                                             cc == bi ? -ei : (cc == bj ? -ej : smi2[rec2 + cc].y));
             f += bd;
             ++moves;
+            pa = bi;
+            pb = bj;
             group_sync<TPC>(grp);
         }
 

@@ -298,6 +298,7 @@ def gpu_line(args):
     value = job_throughput(S * args.steps, world, dev_ms_max)
 
     pairs = st1["two_opt_pairs"] - st0["two_opt_pairs"]
+    evaluated = st1["two_opt_evaluated"] - st0["two_opt_evaluated"]
     moves = st1["two_opt_moves"] - st0["two_opt_moves"]
     two_ms = timing["ms"]["two_opt"]
     launches = sum(timing["launches"].values())
@@ -308,11 +309,14 @@ def gpu_line(args):
                   for mb in (8, 16, 24)}
         l2 = max(probes.values())
         bpp = BYTES_PER_SWAP_PAIR if node_swap else BYTES_PER_PAIR
-        achieved = bpp * pairs / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
+        # bytes of the pairs the kernel evaluated (a pass skips the rows the
+        # last move left unchanged), not of the pairs a plain scan would take
+        achieved = bpp * evaluated / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
         traffic = None if node_swap else two_opt_traffic(inst.name)
         roofline = {
             "kernel": "node_swap_tiled_kernel" if node_swap else "two_opt_tiled_kernel",
-            "bound": "l2", "bytes_per_pair": bpp, "achieved": achieved, "peak": l2,
+            "bound": "l2", "bytes_per_pair": bpp, "pairs_evaluated": evaluated,
+            "achieved": achieved, "peak": l2,
             "unit": "GB/s", "frac": achieved / l2 if l2 else None,
             "traffic": traffic,
             "peak_source": "L2 read bandwidth measured in this run by dpso_probe_l2_read_gbs "
@@ -365,6 +369,7 @@ def gpu_line(args):
                        "parallelism": "replicas" if world > 1 else "single"},
             "two_opt_pairs_per_s": pairs / (two_ms / 1e3) if two_ms > 0 else 0.0,
             "two_opt_moves_applied": moves, "two_opt_pairs": pairs,
+            "two_opt_pairs_evaluated": evaluated,
             "phase_ms": phases, "wall_s": wall,
             "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": sampler.summary(),

@@ -97,11 +97,17 @@ typedef struct dpso_stats {
     int32_t iterations;     /* generations completed */
     int32_t stalled;        /* 1 once stall_limit stopped the loop */
     int64_t gbest_cost;     /* current gbest tour cost */
-    int64_t two_opt_pairs;  /* 2-opt candidate pairs evaluated */
+    int64_t two_opt_pairs;  /* candidate pairs a plain best-improvement scan
+                               evaluates: passes x n(n-3)/2 per tour */
     int64_t two_opt_moves;  /* 2-opt moves applied */
     int64_t two_opt_runs;   /* generations in which the edge exchange ran */
     int32_t device_status;  /* sticky device-side error code (DPSO_OK if none) */
     int32_t reserved;
+    int64_t two_opt_evaluated; /* candidate pairs the kernels evaluated: at most
+                                  two_opt_pairs, fewer when a pass reuses the
+                                  previous pass's row minima (rows a move left
+                                  unchanged are not evaluated again); a count
+                                  of this process's work, not saved in a state */
 } dpso_stats;
 
 /* Per-phase device time of a swarm's generations while timing is on

@@ -73,6 +73,7 @@ struct Ctl {
     unsigned long long pairs;  // 2-opt candidate pairs evaluated
     unsigned long long moves;  // 2-opt moves applied
     unsigned long long runs;   // generations with an edge exchange
+    unsigned long long evals;  // candidate pairs the exchange kernels evaluated
     long long* hist;           // gbest cost after each generation
     int hist_cap;
     int pad1;
@@ -194,6 +195,10 @@ struct TwoOptTask {
     // on it, only the time the last tour finishes does.
     const int* order;
     int kind;  // exchange neighbourhood: 0 edge exchange (2-opt), 1 node swap
+    // Optional: receives the candidate pairs the kernel actually evaluated
+    // (fewer than *pairs, the pairs a plain best-improvement pass scans, when
+    // the kernel reuses the previous pass's row minima).
+    unsigned long long* evals;
 };
 
 // One persistent launch over every tour of several problems: tasks[nprob] and

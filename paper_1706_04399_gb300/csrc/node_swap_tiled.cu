@@ -276,6 +276,7 @@ __global__ void __launch_bounds__(kThreads, 3) node_swap_tiled_kernel(TwoOptBatc
                 atomicAdd(a.pairs, static_cast<unsigned long long>(passes) * npairs);
                 atomicAdd(a.moves, static_cast<unsigned long long>(moves));
             }
+            if (a.evals) atomicAdd(a.evals, static_cast<unsigned long long>(passes) * npairs);
             s_pf = a.pbest ? a.pcost[p] : LLONG_MIN;
         }
         __syncthreads();

@@ -150,6 +150,7 @@ TwoOptTask swarm_task(const dpso_swarm* s) {
     a.pairs = &s->ctl->pairs;
     a.moves = &s->ctl->moves;
     a.status = &s->ctl->status;
+    a.evals = &s->ctl->evals;
     a.order = s->order;
     a.kind = (s->k.flags & DPSO_FLAG_NODE_SWAP) ? 1 : 0;
     return a;
@@ -687,6 +688,7 @@ int dpso_get_stats(dpso_swarm* s, dpso_stats* out) {
     out->two_opt_pairs = static_cast<int64_t>(c.pairs);
     out->two_opt_moves = static_cast<int64_t>(c.moves);
     out->two_opt_runs = static_cast<int64_t>(c.runs);
+    out->two_opt_evaluated = static_cast<int64_t>(c.evals);
     out->device_status = c.status;
     return DPSO_OK;
 }
@@ -1053,6 +1055,7 @@ int autotune_class(dpso_batch* b, dpso_batch::TwoOptClass& cl, cudaStream_t st) 
         t.status = status;
         t.max_moves = kProbeMoves;
         t.order = nullptr;
+        t.evals = nullptr;
     }
     if ((st2 = dalloc(&dtasks, tasks.size(), st))) return cleanup(st2);
     if (cudaMemcpyAsync(dtasks, tasks.data(), sizeof(TwoOptTask) * tasks.size(),

@@ -193,6 +193,7 @@ __global__ void __launch_bounds__(kWarps * 32) two_opt_kernel(TwoOptBatch b) {
                 atomicAdd(a.pairs, static_cast<unsigned long long>(passes) * npairs);
                 atomicAdd(a.moves, static_cast<unsigned long long>(moves));
             }
+            if (a.evals) atomicAdd(a.evals, static_cast<unsigned long long>(passes) * npairs);
             s_pf = a.pbest ? a.pcost[p] : LLONG_MIN;
         }
         __syncthreads();

@@ -259,6 +259,7 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         unsigned long long* const tk = rowkey + ((n + 1) & ~1) + half * 64;
         for (int r = tid; r < TG * 64; r += GT) rowkey[((n + 1) & ~1) + r] = ~0ull;
         int pa = -1, pb = -1;  // the previous move; pb < 0: evaluate every pair
+        unsigned long long evals = 0;  // pairs evaluated (lane 0 of a subgroup's warp 0)
         group_sync<TPC>(grp);
 
         // Warp 0 of a subgroup folds the finished tile at I (parity par) into
@@ -322,6 +323,15 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                 }
                 const int ngroups = cstop > cstart ? (cstop - cstart + 3) >> 2 : 0;
                 const int g0 = (ngroups * wsg) / WSG, g1 = (ngroups * (wsg + 1)) / WSG;
+                if (wsg == 0) {
+                    // pairs (i, j), i+2 <= j <= n-1, (i, j) != (0, n-1), in the
+                    // columns evaluated: cstart .. E-1
+                    const int E = min(cstart + 4 * ngroups, n);
+                    int cnt = row_ok ? max(0, E - max(cstart, i + 2)) : 0;
+                    cnt -= (i == 0 && E == n && cnt > 0) ? 1 : 0;
+                    const unsigned s = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(cnt));
+                    evals += s;
+                }
                 // first valid column of this lane's row (rows past n-3 have none)
                 const int lim = row_ok ? i + 2 : INT_MAX;
                 int m = INT_MAX, cm = 0;
@@ -433,6 +443,7 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
             group_sync<TPC>(grp);
         }
 
+        if (wsg == 0 && lane == 0 && a.evals && evals) atomicAdd(a.evals, evals);
         for (int i = tid; i < n; i += GT) tour[i] = smu[xs16 + i];
         if (tid == 0) {
             a.cost[p] = f;

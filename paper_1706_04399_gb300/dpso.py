@@ -57,7 +57,8 @@ class dpso_stats(ctypes.Structure):
     _fields_ = [("iterations", ctypes.c_int32), ("stalled", ctypes.c_int32),
                 ("gbest_cost", ctypes.c_int64), ("two_opt_pairs", ctypes.c_int64),
                 ("two_opt_moves", ctypes.c_int64), ("two_opt_runs", ctypes.c_int64),
-                ("device_status", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+                ("device_status", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("two_opt_evaluated", ctypes.c_int64)]
 
 
 PHASES = ("move", "mutation", "gbest", "two_opt")

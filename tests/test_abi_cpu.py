@@ -96,3 +96,35 @@ def test_server_host_side_checks(libpath):
     assert L.dpso_server_footprint(ctypes.byref(r), ctypes.byref(out)) == dpso.ERR_ARG
     r.n = dpso.MAX_N + 1
     assert L.dpso_server_footprint(ctypes.byref(r), ctypes.byref(out)) == dpso.ERR_RANGE
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """Every struct the Python binding mirrors has the header's size and field
+    offsets (a C program compiled against include/dpso.h prints them)."""
+    import shutil
+    import subprocess
+    from paper_1706_04399_gb300 import dpso
+    cc = shutil.which("cc") or shutil.which("gcc")
+    if cc is None:
+        pytest.skip("no C compiler")
+    structs = [getattr(dpso, name) for name in dir(dpso)
+               if name.startswith("dpso_") and isinstance(getattr(dpso, name), type)
+               and issubclass(getattr(dpso, name), ctypes.Structure)]
+    assert len(structs) >= 9
+    lines = ['#include <stdio.h>', '#include <stddef.h>', '#include "dpso.h"', "int main(void) {"]
+    for s in structs:
+        lines.append(f'printf("{s.__name__} %zu\\n", sizeof({s.__name__}));')
+        for f, _ in s._fields_:
+            lines.append(f'printf("{s.__name__}.{f} %zu\\n", offsetof({s.__name__}, {f}));')
+    lines.append("return 0; }")
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines))
+    exe = tmp_path / "layout"
+    subprocess.run([cc, "-I", os.path.join(ROOT, "include"), str(src), "-o", str(exe)], check=True)
+    got = dict(line.rsplit(" ", 1) for line in
+               subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+               if line)
+    for s in structs:
+        assert int(got[s.__name__]) == ctypes.sizeof(s), s.__name__
+        for f, _ in s._fields_:
+            assert int(got[f"{s.__name__}.{f}"]) == getattr(s, f).offset, (s.__name__, f)

@@ -254,3 +254,28 @@ def test_side_stream_matches_default_stream():
                                 inst.seed, inst.iterations)
     assert cost == want["gf"] and np.array_equal(tour, want["G"].astype(np.int32))
     ref.close()
+
+
+@pytest.mark.parametrize("n", [60, 300])
+def test_two_opt_evaluated_pair_count(n):
+    """The exchange kernels' evaluated-pair count: each tour's first pass in a
+    generation scans all n(n-3)/2 pairs and later passes only the rows and
+    columns the previous move changed, so runs*S*n(n-3)/2 <= evaluated <=
+    pairs (the plain scan's count, which the oracle reproduces); the node
+    swap rescans every pair."""
+    inst = inputs.random_instance(n, 3, 900 + n)
+    C = cost_matrix_gpu(inst)
+    S, T = 64, 4
+    sw = dpso.Swarm(C, n, inst.tags, dpso.default_params(swarm=S), 3)
+    sw.step(T)
+    st = sw.stats()
+    first_passes = st["two_opt_runs"] * S * (n * (n - 3) // 2)
+    assert st["two_opt_moves"] > 0
+    assert first_passes <= st["two_opt_evaluated"] < st["two_opt_pairs"]
+    sw.close()
+    ns = dpso.Swarm(C, n, inst.tags,
+                    dpso.default_params(swarm=S, flags=dpso.FLAGS_ALL | dpso.FLAG_NODE_SWAP), 3)
+    ns.step(T)
+    st = ns.stats()
+    assert st["two_opt_evaluated"] == st["two_opt_pairs"] > 0
+    ns.close()

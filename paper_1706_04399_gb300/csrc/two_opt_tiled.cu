@@ -6,11 +6,13 @@
 //   the applied move is the smallest (delta, i, j) with delta < 0.
 //
 // Layout and mapping:
-//  * One CTA per tour (persistent grid, work queue), 8 warps.
+//  * A persistent grid takes tours from a work queue; a tour is solved by 8
+//    warps (8 / TPC when a CTA holds TPC short tours, 16 when two tile
+//    subgroups of 8 warps evaluate two tiles of a pass at once).
 //  * A tile is R positions I..I+R-1 (R = 32 or 30; fewer for long tours), one
 //    per lane; its R+1 cost rows C[x_I..x_I+R] are staged in shared memory,
-//    one bulk copy per row posted by one lane of the group's first warp and
-//    counted on an mbarrier (a tile costs a handful of instructions instead
+//    one bulk copy per row, posted by a few lanes of every warp of the group
+//    and counted on an mbarrier (a tile costs a handful of instructions instead
 //    of one 16-byte copy per lane-chunk).
 //  * 16-byte copies need 16-byte-aligned rows, which alone would put rows a,
 //    a+8, a+16, a+24 in the same bank.  The cost matrix is therefore kept in
@@ -24,11 +26,14 @@
 //    the minimum of C[x_i][x_c] + C[x_i+1][x_c+1] - C[x_c][x_c+1] and the
 //    first group holding it, with selects only (no divergent branch in the
 //    column loop).  Subtracting C[x_i][x_i+1] gives a candidate (delta, i,
-//    group); a packed 64-bit key keeps the lexicographically smallest across
-//    tiles, and when a tile's candidate wins, its exact column and the two
-//    gathered costs are read back from the still-staged tile.
-//    One block reduction per pass yields (delta*, i*, j*), and the winning
-//    lane publishes C[x_i*][x_j*] and C[x_i*+1][x_j*+1], the two new edges.
+//    group) as a packed 64-bit key; the warps of a tile fold theirs per row.
+//  * Row cache: each row's smallest key survives from pass to pass.  A move
+//    that reverses positions a+1..b changes the deltas of rows a..b, and of
+//    rows below a only in columns a..b, so the next pass re-evaluates the
+//    tiles of rows a..b in full, the tiles below a only in the groups that
+//    cover a..b (in full where a row's cached minimum lies in them), and
+//    skips the tiles past b.  The pass's move is the smallest cached key; its
+//    exact column and the two new edge costs are read from C.
 //  * Pairs with j = i+1 and (0, n-1) have delta = 0 for a symmetric C and
 //    never win, so only the triangle at the start of each tile is masked.
 #include <climits>
@@ -59,8 +64,8 @@ size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages) {
         static_cast<size_t>(stages) * (rows_per_tile + 1) * shifted_ld(n) * sizeof(int);
     const size_t rec = static_cast<size_t>(n + 4) * sizeof(int2);
     const size_t xs = static_cast<size_t>((n + 1 + 7) / 8 * 8) * sizeof(uint16_t);
-    // the row cache and, per tile subgroup, two 32-key fold buffers
-    const size_t cache = (static_cast<size_t>((n + 1) & ~1) + 64 * stages) * sizeof(uint64_t);
+    // the row cache
+    const size_t cache = static_cast<size_t>((n + 1) & ~1) * sizeof(uint64_t);
     return rows + rec + xs + cache;
 }
 
@@ -130,8 +135,10 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
     // (n + 4 int2, the last four padding), then the tour (n + 1 uint16).
     // Offsets depend on the tour's n; slices are sized for the largest n.
     extern __shared__ __align__(128) int sm_all[];
-    __shared__ unsigned long long s_key[kWarps * TG];
     __shared__ unsigned long long s_best[TPC];
+    __shared__ unsigned int s_next[TPC];     // tiles taken in this pass (TG = 2)
+    __shared__ int s_tile[TPC * TG * 2];     // a subgroup's next tile, by parity
+    __shared__ int s_mode[TPC * TG];         // 1: the subgroup's tile is full
     __shared__ int s_part[TPC], s_e0[TPC], s_e1[TPC];
     __shared__ long long s_pf[TPC];
     // tile-arrival barrier per tile subgroup; a subgroup whose tile copy did
@@ -150,7 +157,6 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
     int2* smi2 = reinterpret_cast<int2*>(smi);
     const int4* smi4 = reinterpret_cast<const int4*>(smi);
     uint16_t* smu = reinterpret_cast<uint16_t*>(smi);
-    unsigned long long* s_keyg = s_key + grp * WPT;
 
     const int sg = grp * TG + half;  // this thread's tile subgroup slot
     const unsigned mbar = smem_addr(&s_mbar[sg]);
@@ -191,30 +197,27 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
         const int guard = 1000 + 100 * n;
 
-        // Warp 0 of the subgroup stages the cost rows of the tile starting at I:
-        // lane r posts row r as one bulk copy (row r from shifted copy
-        // (r>>3)&3); lane 0 first arms the barrier with the tile's bytes.
-        // Offsets into the shifted copies fit 32 bits (4 n ldq words < 2^30).
+        // The subgroup stages the `count` cost rows of the tile starting at I:
+        // each warp posts kPerWarp rows, one bulk copy per lane (row r from
+        // shifted copy (r>>3)&3), so the copies are issued by several warps at
+        // once rather than one after another by one warp.  Lane 0 of warp 0
+        // arms the barrier with the tile's bytes afterwards (a copy that lands
+        // before that only takes the transaction count below zero: the phase
+        // still waits for that one arrival).  Offsets into the shifted copies
+        // fit 32 bits (4 n ldq words < 2^30).
+        constexpr int kPerWarp = (kStaged + WSG - 1) / WSG;
         const char* const cs0 = reinterpret_cast<const char*>(a.Cs);
         const unsigned tile_s = smem_addr(smi + half * buf_words);
         const unsigned row_bytes = static_cast<unsigned>(ldq) * 4u;
-        auto stage = [&](int I) {
-            const int count = min(kStaged, n - 1 - I);
-            if (wsg == 0) {
-                // the subgroup barrier before this ordered the generic reads of
-                // the previous tile; this orders them before the async writes
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                if (lane == 0)
-                    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(mbar),
-                                 "r"(static_cast<unsigned>(count) * row_bytes)
-                                 : "memory");
-                __syncwarp();
-                for (int r = lane; r < count; r += 32) {
-                    const unsigned k = (r >> 3) & 3;
-                    const unsigned off =
-                        (k * static_cast<unsigned>(n) + smu[xs16 + I + r]) * row_bytes;
-                    bulk_row(tile_s + r * row_bytes, cs0 + off, row_bytes, mbar);
-                }
+        auto stage = [&](int I, int count) {
+            // the subgroup barrier before this ordered the generic reads of
+            // the previous tile; this orders them before the async writes
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            const int r = wsg * kPerWarp + lane;
+            if (lane < kPerWarp && r < count) {
+                const unsigned k = (r >> 3) & 3;
+                const unsigned off = (k * static_cast<unsigned>(n) + smu[xs16 + I + r]) * row_bytes;
+                bulk_row(tile_s + r * row_bytes, cs0 + off, row_bytes, mbar);
             }
         };
         // Every thread waits for the tile's bytes, at most ~2 s of clock; a
@@ -250,29 +253,18 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         group_sync<TPC>(grp);
 
         // Row cache: rowkey[i] is the smallest (delta, i, group) of row i over
-        // all its columns, from the last pass that evaluated it.  A move that
+        // all its columns, as of the last pass that evaluated it.  A move that
         // reverses positions pa+1..pb changes the pairs of rows pa..pb and,
         // for rows below pa, only columns pa..pb; rows above pb keep theirs.
-        // tk: per subgroup, two 32-entry buffers (by tile parity) where the
-        // subgroup's warps fold their keys for the rows of a tile.
+        // The warps of a tile fold their keys into it with shared atomicMin.
         unsigned long long* const rowkey = reinterpret_cast<unsigned long long*>(smi) + rk64;
-        unsigned long long* const tk = rowkey + ((n + 1) & ~1) + half * 64;
-        for (int r = tid; r < TG * 64; r += GT) rowkey[((n + 1) & ~1) + r] = ~0ull;
         int pa = -1, pb = -1;  // the previous move; pb < 0: evaluate every pair
         unsigned long long evals = 0;  // pairs evaluated (lane 0 of a subgroup's warp 0)
+        if (tid == 0) {
+            s_best[grp] = ~0ull;
+            s_next[grp] = 0;
+        }
         group_sync<TPC>(grp);
-
-        // Warp 0 of a subgroup folds the finished tile at I (parity par) into
-        // the row cache: a full tile replaces the rows' keys, a partial one
-        // (only the changed columns evaluated) takes the smaller.
-        auto combine = [&](int I, bool partial, int par) {
-            const int i = I + lane;
-            if (lane < kRows && i <= n - 3) {
-                const unsigned long long v = tk[par * 32 + lane];
-                rowkey[i] = partial ? min(rowkey[i], v) : v;
-            }
-            tk[par * 32 + lane] = ~0ull;
-        };
 
         for (;;) {
             if (a.max_moves > 0 && moves >= a.max_moves) break;
@@ -282,29 +274,46 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
             }
             const bool first = pb < 0;
             const int tlast = first ? ntiles - 1 : min(ntiles - 1, pb / kRows);
-            int prevI = -1, par = 0;
-            bool prevPartial = false;
-            for (int t = half; t <= tlast; t += TG) {
-                const int I = t * kRows;
+            // Tiles are taken from the last one down (the tiles that need every
+            // column come first); with two subgroups each takes the next one
+            // when it finishes its own (s_tile, double-buffered by tile parity,
+            // published before the subgroup barrier that the readers pass).
+            int par = 0, taken = 0;
+            if (TG == 2 && wsg == 0 && lane == 0)
+                s_tile[sg * 2] = tlast - static_cast<int>(atomicAdd(&s_next[grp], 1u));
+            for (;;) {
                 half_sync<TPC, TG>(grp, half);  // the previous tile is no longer read
                 if (s_abort[sg]) break;  // read after the barrier: the subgroup agrees
-                if (wsg == 0 && prevI >= 0) combine(prevI, prevPartial, par ^ 1);
-                stage(I);
-                // the tile's mode: rows pa..pb (or the first pass) need every
-                // column; rows below pa only pa..pb, unless a row's cached
-                // minimum sits in a group that touches pa..pb
+                const int t = TG == 1 ? tlast - taken : s_tile[sg * 2 + par];
+                if (t < 0) break;
+                ++taken;
+                const int I = t * kRows;
+                const int count = min(kStaged, n - 1 - I);
+                stage(I, count);
                 const int i = I + lane;
                 const bool row_ok = lane < kRows && i <= n - 3;
-                bool full = first || (I <= pb && I + kRows - 1 >= pa);
-                if (!full) {
-                    bool need = false;
-                    if (row_ok) {
-                        const int cmc = static_cast<int>(rowkey[i] & 0xffffu);
-                        need = cmc + 3 >= pa && cmc <= pb;
+                if (wsg == 0) {
+                    // the tile's mode: rows pa..pb (or the first pass) need every
+                    // column; rows below pa only pa..pb, unless a row's cached
+                    // minimum sits in a group that touches pa..pb.  A full tile
+                    // starts its rows' keys afresh.  Both happen before the
+                    // barrier arrival that the other warps acquire.
+                    bool full = first || (I <= pb && I + kRows - 1 >= pa);
+                    if (!full) {
+                        bool need = false;
+                        if (row_ok) {
+                            const int cmc = static_cast<int>(rowkey[i] & 0xffffu);
+                            need = cmc + 3 >= pa && cmc <= pb;
+                        }
+                        full = __any_sync(0xffffffffu, need);
                     }
-                    full = __any_sync(0xffffffffu, need);  // same rows in every warp
+                    if (full && row_ok) rowkey[i] = ~0ull;
+                    if (lane == 0) s_mode[sg] = full ? 1 : 0;
+                    __syncwarp();
+                    if (lane == 0) mbar_expect(mbar, static_cast<unsigned>(count) * row_bytes);
                 }
                 stage_wait();
+                const bool full = s_mode[sg] != 0;
                 // lanes past the tile height idle on a valid row; byte offsets
                 // of this lane's two rows (row start plus its 0..3 word shift)
                 const int ra = min(lane, kRows - 1), rb1 = min(lane + 1, kRows);
@@ -329,8 +338,7 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                     const int E = min(cstart + 4 * ngroups, n);
                     int cnt = row_ok ? max(0, E - max(cstart, i + 2)) : 0;
                     cnt -= (i == 0 && E == n && cnt > 0) ? 1 : 0;
-                    const unsigned s = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(cnt));
-                    evals += s;
+                    evals += __reduce_add_sync(0xffffffffu, static_cast<unsigned>(cnt));
                 }
                 // first valid column of this lane's row (rows past n-3 have none)
                 const int lim = row_ok ? i + 2 : INT_MAX;
@@ -366,25 +374,20 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                 while (c < cmask) group(true);
                 while (c < cend) group(false);
                 if (m != INT_MAX && row_ok)
-                    atomicMin(&tk[par * 32 + lane], pack_key(m + smi2[rec2 + i].y, i, cm));
-                prevI = I;
-                prevPartial = !full;
+                    atomicMin(&rowkey[i], pack_key(m + smi2[rec2 + i].y, i, cm));
+                if (TG == 2 && wsg == 0 && lane == 0)
+                    s_tile[sg * 2 + (par ^ 1)] =
+                        tlast - static_cast<int>(atomicAdd(&s_next[grp], 1u));
                 par ^= 1;
             }
             ++passes;
             group_sync<TPC>(grp);
             if (tour_aborted()) break;  // no move from a pass with a missing tile
-            if (wsg == 0 && prevI >= 0) combine(prevI, prevPartial, par ^ 1);
-            group_sync<TPC>(grp);
-            unsigned long long kl = ~0ull;
-            for (int r = tid; r <= n - 3; r += GT) kl = min(kl, rowkey[r]);
-            const unsigned long long kw = warp_min_u64(kl);
-            if (lane == 0) s_keyg[warp] = kw;
-            group_sync<TPC>(grp);
-            if (warp == 0) {
-                unsigned long long kk = lane < WPT ? s_keyg[lane] : ~0ull;
-                kk = warp_min_u64(kk);
-                if (lane == 0) s_best[grp] = kk;
+            {
+                unsigned long long kl = ~0ull;
+                for (int r = tid; r <= n - 3; r += GT) kl = min(kl, rowkey[r]);
+                kl = warp_min_u64(kl);
+                if (lane == 0 && kl != ~0ull) atomicMin(&s_best[grp], kl);
             }
             group_sync<TPC>(grp);
             const unsigned long long best = s_best[grp];
@@ -392,27 +395,25 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
             const int bd = static_cast<int>(static_cast<uint32_t>(best >> 32) ^ 0x80000000u);
             if (bd >= 0) break;
             const int bi = static_cast<int>((best >> 16) & 0xffffu);
-            if (tid == 0) {
+            if (warp == 0) {
                 // the winning group's first column of delta bd, with the two
-                // costs of the new edges, from C
-                const int cmg = static_cast<int>(best & 0xffffu);
-                const int xi = smu[xs16 + bi], xi1 = smu[xs16 + bi + 1];
-                int jx = -1, e0 = 0, e1 = 0;
-                for (int u = 0; u < 4 && jx < 0; ++u) {
-                    const int j = cmg + u;
-                    if (j < bi + 2 || j > n - 1) continue;
+                // costs of the new edges, from C: lanes 0..3 test one column each
+                const int j = static_cast<int>(best & 0xffffu) + lane;
+                bool match = false;
+                int e0 = 0, e1 = 0;
+                if (lane < 4 && j >= bi + 2 && j <= n - 1) {
+                    const int xi = smu[xs16 + bi], xi1 = smu[xs16 + bi + 1];
                     const int xj = smu[xs16 + j], xj1 = smu[xs16 + j + 1];
-                    const int a_ = C[static_cast<size_t>(xi) * ldc + xj];
-                    const int b_ = C[static_cast<size_t>(xi1) * ldc + xj1];
-                    if (a_ + b_ + smi2[rec2 + j].y + smi2[rec2 + bi].y == bd) {
-                        jx = j;
-                        e0 = a_;
-                        e1 = b_;
-                    }
+                    e0 = C[static_cast<size_t>(xi) * ldc + xj];
+                    e1 = C[static_cast<size_t>(xi1) * ldc + xj1];
+                    match = e0 + e1 + smi2[rec2 + j].y + smi2[rec2 + bi].y == bd;
                 }
-                s_part[grp] = jx;  // (the work item is no longer needed this tour)
-                s_e0[grp] = e0;
-                s_e1[grp] = e1;
+                const unsigned mm = __ballot_sync(0xffffffffu, match);
+                if (lane == (mm ? __ffs(mm) - 1 : 0)) {
+                    s_part[grp] = mm ? j : -1;  // (the work item is no longer needed this tour)
+                    s_e0[grp] = e0;
+                    s_e1[grp] = e1;
+                }
             }
             group_sync<TPC>(grp);
             const int bj = s_part[grp];
@@ -420,6 +421,10 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
             if (bj < 0) {  // cannot happen: the cache and C disagree
                 if (tid == 0 && a.status) atomicExch(a.status, DPSO_ERR_INTERNAL);
                 break;
+            }
+            if (tid == 0) {  // every thread has read them; the next pass starts afresh
+                s_best[grp] = ~0ull;
+                s_next[grp] = 0;
             }
             // reverse x[bi+1..bj] and the edge terms strictly between bi and bj
             for (int q2 = tid; q2 < (bj - bi) / 2; q2 += GT) {
@@ -513,40 +518,38 @@ int two_opt_tiled_ctas(int n, int rows, int tpc, int tg) {
     return min(by_smem, tg == 2 ? 2 : (rows == 30 ? 4 : 3));
 }
 
-// Default launch shape for tours of n viewpoints, from sweeps on GB300 of full
-// 2-opt runs on random tours (n = 50 .. 2000, enough tours to fill the GPU):
-// 32-row tiles with 4 tours per CTA up to n = 128; 30-row tiles (held to 64
-// registers so that four CTAs share an SM) with 2 tours per CTA up to 256 and
-// with 1 while four such CTAs fit; beyond that the tallest of 32 / 24 / 16 / 8
-// rows that fits in 220 KB, except that 24 rows win over a 32-row tile that
-// leaves a single CTA per SM when they allow two.  One buffer per tile: at
-// the sizes measured, more resident CTAs beat a deeper copy pipeline.
-// two_opt_tiled_rows returns 0 when no tile height fits.
-int two_opt_tiled_rows(int n) {
-    if (n < 3 || n > 65535) return 0;
-    if (n <= 128) return 32;
-    if (two_opt_tiled_ctas(n, 30, n <= 256 ? 2 : 1, 1) >= 4) return 30;
-    for (int rows : {32, 24, 16, 8}) {
-        if (two_opt_tiled_smem(n, rows, 1) > 220 * 1024) continue;
-        if (rows == 32 && two_opt_tiled_ctas(n, 32, 1, 1) == 1 &&
-            two_opt_tiled_smem(n, 24, 1) <= 220 * 1024 && two_opt_tiled_ctas(n, 24, 1, 1) >= 2)
-            return 24;
-        return rows;
-    }
-    return 0;
+// Default launch shape for tours of n viewpoints, from sweeps on GB300 of
+// steady-state DPSO generations (1024 tours, n = 64 .. 1992): up to n = 256,
+// 32-row tiles with 2 tours per CTA; beyond that, one tour per CTA and the
+// tile height and tile subgroups that keep the most tile rows in flight per
+// SM (rows x subgroups x resident CTAs), ties to the taller tile and to one
+// subgroup.  With the row cache most tiles of a pass re-evaluate a few
+// columns, so a pass costs about its staged rows, and more rows in flight
+// hide more of each tile's copy.  two_opt_tiled_rows returns 0 when no tile
+// height fits.
+int two_opt_tiled_tg(int n, int rows, int tpc) {
+    if (tpc != 1 || n <= 256 || !two_opt_tiled_fits(n, rows, 1, 2)) return 1;
+    return 2 * two_opt_tiled_ctas(n, rows, 1, 2) > two_opt_tiled_ctas(n, rows, 1, 1) ? 2 : 1;
 }
 
-// Tiles of one tour in flight for the default shape: 2 for 30-row tiles with
-// one tour per CTA when two such 16-warp CTAs fit in an SM (measured on the
-// facade generation: 10.9 vs 11.6 ms), else 1.
-int two_opt_tiled_tg(int n, int rows, int tpc) {
-    return rows == 30 && tpc == 1 && two_opt_tiled_ctas(n, 30, 1, 2) >= 2 ? 2 : 1;
+int two_opt_tiled_rows(int n) {
+    if (n < 3 || n > 65535) return 0;
+    if (n <= 256) return 32;
+    int best = 0, best_score = 0;
+    for (int rows : {32, 30, 24, 16, 8}) {
+        if (!two_opt_tiled_fits(n, rows, 1, 1)) continue;
+        const int tg = two_opt_tiled_tg(n, rows, 1);
+        const int score = rows * tg * two_opt_tiled_ctas(n, rows, 1, tg);
+        if (score > best_score) {
+            best = rows;
+            best_score = score;
+        }
+    }
+    return best;
 }
 
 int two_opt_tiled_tpc(int n, int rows) {
-    int tpc = n <= 128 ? 4 : (n <= 256 ? 2 : 1);
-    while (tpc > 1 && group_bytes(n, rows, 1) * tpc > 220 * 1024) tpc /= 2;
-    return tpc;
+    return n <= 256 && two_opt_tiled_fits(n, rows, 2, 1) ? 2 : 1;
 }
 
 cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStream_t st) {

@@ -42,6 +42,15 @@ CPU_SAMPLE_SWARM = 16       # oracle sample: particles
 CPU_SAMPLE_GENERATIONS = 10 # oracle sample: generations
 
 
+def cpu_sample_shape(n: int, node_swap: bool = False) -> tuple[int, int]:
+    """(particles, generations) of the oracle sample, sized to a few tens of
+    seconds on one core: the oracle's first generations cost about n^3 per
+    particle (2-opt from the initial tours), the node swap about twice that."""
+    if n > 600:
+        return 4, 1
+    return CPU_SAMPLE_SWARM, (4 if node_swap else CPU_SAMPLE_GENERATIONS)
+
+
 def _env_int(name, default):
     try:
         return int(os.environ.get(name, default))
@@ -103,15 +112,16 @@ def run_reference(args):
     per_step = []
     import oracle
     C, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
-    sw = oracle.Swarm(C, inst.tags, swarm=CPU_SAMPLE_SWARM, seed=inst.seed)
+    swarm, _ = cpu_sample_shape(inst.n)
+    sw = oracle.Swarm(C, inst.tags, swarm=swarm, seed=inst.seed)
     sw.run(args.warmup)
     for _ in range(args.steps):
         t0 = time.perf_counter()
         sw.iterate()
         per_step.append(time.perf_counter() - t0)
     total = sum(per_step)
-    value = CPU_SAMPLE_SWARM * args.steps / total
-    sample = (f"{inst.name} instance (n={inst.n}), oracle swarm of {CPU_SAMPLE_SWARM} particles "
+    value = swarm * args.steps / total
+    sample = (f"{inst.name} instance (n={inst.n}), oracle swarm of {swarm} particles "
               f"instead of {inst.swarm}, {args.warmup} untimed + {args.steps} timed generations")
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
@@ -328,10 +338,11 @@ def gpu_line(args):
         }
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cval, csec = oracle_sample(inst, CPU_SAMPLE_SWARM, 0, CPU_SAMPLE_GENERATIONS, flags)
+            cs, cg = cpu_sample_shape(n, node_swap)
+            cval, csec = oracle_sample(inst, cs, 0, cg, flags)
             cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{inst.name} instance (n={n}), oracle swarm of {CPU_SAMPLE_SWARM} "
-                             f"particles, first {CPU_SAMPLE_GENERATIONS} generations "
+                   "sample": f"{inst.name} instance (n={n}), oracle swarm of {cs} "
+                             f"particles, first {cg} generations "
                              f"({csec:.1f} s)",
                    "host_cores": cpu_cores(), "cpu": cpu_model()}
         e2e = None

@@ -78,22 +78,23 @@ __global__ void __launch_bounds__(kThreads, 3) node_swap_tiled_kernel(TwoOptBatc
         const unsigned tile_s = smem_addr(smi);
         const unsigned row_bytes = static_cast<unsigned>(ldq) * 4u;
 
-        // Warp 0 stages rows of positions I-1 .. I+R (I-1 wrapping): lane r
-        // posts staged row r from shifted copy (r>>3)&3.
+        // The block stages rows of positions I-1 .. I+R (I-1 wrapping), staged
+        // row r from shifted copy (r>>3)&3: each warp posts kPerWarp rows, one
+        // bulk copy per lane, so the copies are issued by all warps at once;
+        // lane 0 of warp 0 arms the barrier (a copy that lands first only
+        // takes the transaction count below zero until that one arrival).
+        constexpr int kPerWarp = (kStaged + kWarps - 1) / kWarps;
         auto stage = [&](int I) {
             const int count = min(kStaged, n + 1 - I);
-            if (warp == 0) {
-                asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-                if (lane == 0) mbar_expect(mbar, static_cast<unsigned>(count) * row_bytes);
-                __syncwarp();
-                for (int r = lane; r < count; r += 32) {
-                    int pos = I - 1 + r;
-                    if (pos < 0) pos += n;
-                    const unsigned k = (r >> 3) & 3;
-                    const unsigned off =
-                        (k * static_cast<unsigned>(n) + smu[xs16 + pos]) * row_bytes;
-                    bulk_row(tile_s + r * row_bytes, cs0 + off, row_bytes, mbar);
-                }
+            asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+            if (warp == 0 && lane == 0) mbar_expect(mbar, static_cast<unsigned>(count) * row_bytes);
+            const int r = warp * kPerWarp + lane;
+            if (lane < kPerWarp && r < count) {
+                int pos = I - 1 + r;
+                if (pos < 0) pos += n;
+                const unsigned k = (r >> 3) & 3;
+                const unsigned off = (k * static_cast<unsigned>(n) + smu[xs16 + pos]) * row_bytes;
+                bulk_row(tile_s + r * row_bytes, cs0 + off, row_bytes, mbar);
             }
         };
         auto at = [](const char* row, int off) { return *reinterpret_cast<const int*>(row + off); };

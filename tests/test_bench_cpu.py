@@ -98,3 +98,11 @@ def test_instance_sharding_covers_every_instance_once():
     names = [n for part in views[0] for n in part]
     assert sorted(names) == sorted(f"batched{i}" for i in range(10))  # each exactly once
     assert [len(part) for part in views[0]] == [4, 3, 3]
+
+
+def test_oracle_sample_is_bounded_by_instance_size():
+    # the bridge-sized oracle sample stays a few particles and one generation
+    assert bench.cpu_sample_shape(400) == (16, 10)
+    assert bench.cpu_sample_shape(400, node_swap=True) == (16, 4)
+    s, g = bench.cpu_sample_shape(1992)
+    assert s * g <= 4

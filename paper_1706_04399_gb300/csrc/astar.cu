@@ -16,11 +16,13 @@
 //  * Pairs whose voxels lie in different connected components of the free
 //    voxels (union-find over the 26-neighbourhood) are blocked without a
 //    search: A* could only exhaust its open list or its cap there.
-//  * Each search has its own binary heap and open-addressing map (voxel ->
-//    best g, closed; slots stamped by search, so nothing is cleared) in
-//    device scratch.  Pass 1 gives every pair room for 256
-//    expansions; pairs that need more are searched again, from the start,
-//    with room for the full expansion cap.
+//  * Pass 1: one warp per search, its map and open list in shared memory
+//    (astar_warp_kernel); a search that outgrows them is searched again, from
+//    the start, by pass 2: one thread per search with its own binary heap and
+//    open-addressing map (voxel -> best g, closed; slots stamped by search,
+//    so nothing is cleared) in device scratch, room for the full expansion
+//    cap.  Grids or weights too large for the warp pass's packed keys take
+//    the thread pass twice instead: room for 256 expansions, then the cap.
 //  * C[i][j] = C[j][i] = g * unit_mm; blocked_cost where a viewpoint lies
 //    outside the grid or in an occupied voxel, or the cap was exhausted.
 #include <climits>
@@ -267,6 +269,204 @@ __global__ void astar_pairs_kernel(AstarArgs A) {
     A.C[static_cast<size_t>(pr.y) * A.n + pr.x] = static_cast<int>(c);
 }
 
+// The same search with one warp per pair and the whole state in shared
+// memory, for searches that stay small (which, with the squared-distance
+// heuristic, is nearly all of them).  Per warp:
+//   map:  kWarpSlots slots (voxel | closed bit, best g), linear probing with
+//         lanes inserting concurrently by 64-bit CAS (nothing is deleted
+//         within a search, so a lane that finds an empty slot knows its voxel
+//         is not further along);
+//   open: an append-only array of keys (f << 42 | h << 24 | voxel), popped
+//         entries overwritten with ~0.  Keys of live entries are distinct
+//         (a voxel is pushed again only with a smaller g), so the pop is a
+//         warp-wide minimum and its owner lane is unique.
+// A pop, the closed test, the goal and cap tests are uniform over the warp;
+// lanes 0..25 then relax one neighbour each and append their entries in lane
+// order.  The pushes of one expansion are the sequential search's (each
+// neighbour's test reads only its own slot), and the pop order depends only
+// on the set of keys, so the result is the sequential search's.  A search
+// that would outgrow the map or the open array is left to the global pass
+// (retry flag).  Host-checked bounds keep f < 2^22, h < 2^18, voxel < 2^24.
+constexpr int kWarpSlots = 2048;         // map slots per warp
+constexpr int kWarpOpen = 2048;          // open entries per warp
+constexpr int kWarpDistinct = 1900;      // inserts before a search hands over
+constexpr int kWarpsPerBlock = 7;        // 7 x 32 KB of shared memory per block
+constexpr unsigned long long kEmptySlot = ~0ull;
+constexpr unsigned kClosed = 1u << 30;   // closed bit of a slot's voxel word
+
+struct WarpArgs {
+    AstarGrid gr;
+    const unsigned char* occ;
+    const int* vox;
+    const int* comp;
+    const int2* pairs;
+    int npairs;
+    unsigned* queue;  // next pair (zero on entry)
+    int a1, a2, a3;
+    long long unit_mm;
+    int blocked_cost;
+    int max_exp;
+    int* C;
+    int n;
+    int* retry;  // 1: left to the global pass
+    int* err;
+};
+
+__device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
+    return v;
+}
+
+__global__ void __launch_bounds__(32 * kWarpsPerBlock) astar_warp_kernel(WarpArgs A) {
+    extern __shared__ unsigned long long sm_astar[];
+    const int lane = threadIdx.x & 31;
+    unsigned long long* const open = sm_astar + (threadIdx.x >> 5) * (kWarpOpen + kWarpSlots);
+    unsigned long long* const map = open + kWarpOpen;
+    const int nx = A.gr.nx, ny = A.gr.ny, nz = A.gr.nz;
+    const int nxy = nx * ny;
+    // this lane's neighbour offset (lanes 0..25; the 27 offsets minus the centre)
+    const int d = lane < 13 ? lane : lane + 1;
+    const int ddx = d % 3 - 1, ddy = (d / 3) % 3 - 1, ddz = d / 9 - 1;
+    const int step = A.a1 * ddx * ddx + A.a2 * ddy * ddy + A.a3 * ddz * ddz;
+    auto slot0 = [](int v) { return (static_cast<unsigned>(v) * 2654435761u) >> 21; };  // 11 bits
+    for (;;) {
+        int k = 0;
+        if (lane == 0) k = static_cast<int>(atomicAdd(A.queue, 1u));
+        k = __shfl_sync(0xffffffffu, k, 0);
+        if (k >= A.npairs) break;
+        const int2 pr = A.pairs[k];
+        const int s = A.vox[pr.x], t = A.vox[pr.y];
+        long long result = -1;
+        bool handover = false;
+        if (s >= 0 && t >= 0 && A.comp[s] == A.comp[t]) {
+            for (int i = lane; i < kWarpSlots; i += 32) map[i] = kEmptySlot;
+            const int tx = t % nx, ty = (t / nx) % ny, tz = t / nxy;
+            const int sx = s % nx, sy = (s / nx) % ny, sz = s / nxy;
+            const int h0 = (sx - tx) * (sx - tx) + (sy - ty) * (sy - ty) + (sz - tz) * (sz - tz);
+            __syncwarp();
+            if (lane == 0) {
+                map[slot0(s)] = static_cast<unsigned long long>(s) << 32;  // g = 0
+                open[0] = (static_cast<unsigned long long>(h0) << 42) |
+                          (static_cast<unsigned long long>(h0) << 24) | static_cast<unsigned>(s);
+            }
+            int len = 1, distinct = 1, expanded = 0;
+            __syncwarp();
+            for (;;) {
+                // pop the smallest (f, h, voxel)
+                unsigned long long mine = ~0ull;
+                int at = -1;
+                for (int i = lane; i < len; i += 32) {
+                    const unsigned long long key = open[i];
+                    if (key < mine) {
+                        mine = key;
+                        at = i;
+                    }
+                }
+                const unsigned long long top = warp_min_key(mine);
+                if (top == ~0ull) break;  // the open list is exhausted
+                if (mine == top) open[at] = ~0ull;
+                const int v = static_cast<int>(top & 0xffffffu);
+                const int h = static_cast<int>((top >> 24) & 0x3ffffu);
+                const int g = static_cast<int>(top >> 42) - h;
+                // its slot exists (inserted when it was pushed); the probe is
+                // bounded all the same, and a miss hands the pair over
+                unsigned sv = slot0(v);
+                unsigned long long e = map[sv];
+                for (int probe = 1; probe < kWarpSlots &&
+                                    static_cast<int>((e >> 32) & (kClosed - 1)) != v; ++probe) {
+                    sv = (sv + 1) & (kWarpSlots - 1);
+                    e = map[sv];
+                }
+                __syncwarp();
+                if (static_cast<int>((e >> 32) & (kClosed - 1)) != v) {
+                    handover = true;
+                    break;
+                }
+                if (e & (static_cast<unsigned long long>(kClosed) << 32)) continue;  // stale entry
+                if (lane == 0) map[sv] = e | (static_cast<unsigned long long>(kClosed) << 32);
+                if (v == t) {
+                    result = g;
+                    break;
+                }
+                if (expanded >= A.max_exp) break;  // cap: blocked
+                ++expanded;
+                if (distinct + 26 > kWarpDistinct || len + 26 > kWarpOpen) {
+                    handover = true;
+                    break;
+                }
+                const int x = v % nx, y = (v / nx) % ny, z = v / nxy;
+                const int xx = x + ddx, yy = y + ddy, zz = z + ddz;
+                bool push = false, inserted = false, lost = false;
+                unsigned long long key = 0;
+                if (lane < 26 && xx >= 0 && yy >= 0 && zz >= 0 && xx < nx && yy < ny && zz < nz) {
+                    const int u = (zz * ny + yy) * nx + xx;
+                    if (!__ldg(A.occ + u)) {
+                        const int gu = g + step;
+                        const unsigned long long want = (static_cast<unsigned long long>(u) << 32) |
+                                                        static_cast<unsigned>(gu);
+                        unsigned su = slot0(u);
+                        // fewer than kWarpSlots voxels are ever inserted, so an
+                        // empty slot ends the probe within kWarpSlots steps
+                        lost = true;
+                        for (int probe = 0; probe < kWarpSlots; ++probe) {
+                            unsigned long long cur = map[su];
+                            if (cur == kEmptySlot) {
+                                cur = atomicCAS(map + su, kEmptySlot, want);
+                                if (cur == kEmptySlot) {
+                                    inserted = push = true;
+                                    lost = false;
+                                    break;
+                                }
+                            }
+                            if (static_cast<int>((cur >> 32) & (kClosed - 1)) == u) {
+                                if (!(cur & (static_cast<unsigned long long>(kClosed) << 32)) &&
+                                    gu < static_cast<int>(cur & 0xffffffffu)) {
+                                    map[su] = want;
+                                    push = true;
+                                }
+                                lost = false;
+                                break;
+                            }
+                            su = (su + 1) & (kWarpSlots - 1);
+                        }
+                        if (push) {
+                            const int hu = (xx - tx) * (xx - tx) + (yy - ty) * (yy - ty) +
+                                           (zz - tz) * (zz - tz);
+                            key = (static_cast<unsigned long long>(gu + hu) << 42) |
+                                  (static_cast<unsigned long long>(hu) << 24) |
+                                  static_cast<unsigned>(u);
+                        }
+                    }
+                }
+                if (__any_sync(0xffffffffu, lost)) {  // cannot happen (see above)
+                    handover = true;
+                    break;
+                }
+                const unsigned pb = __ballot_sync(0xffffffffu, push);
+                if (push) open[len + __popc(pb & ((1u << lane) - 1u))] = key;
+                len += __popc(pb);
+                distinct += __popc(__ballot_sync(0xffffffffu, inserted));
+                __syncwarp();
+            }
+        }
+        if (lane == 0) {
+            if (handover) {
+                A.retry[k] = 1;
+            } else {
+                long long c = result < 0 ? A.blocked_cost : result * A.unit_mm;
+                if (c > DPSO_COST_MAX) {
+                    atomicOr(A.err, 2);
+                    c = DPSO_COST_MAX;
+                }
+                A.C[static_cast<size_t>(pr.x) * A.n + pr.y] = static_cast<int>(c);
+                A.C[static_cast<size_t>(pr.y) * A.n + pr.x] = static_cast<int>(c);
+            }
+        }
+        __syncwarp();
+    }
+}
+
 // Connected components of the free voxels (26-neighbourhood) by union-find:
 // every root ends at the smallest voxel index of its component whatever the
 // order of the unions (hook the larger root under the smaller by CAS).
@@ -347,6 +547,31 @@ int check_params(const dpso_astar_params* ap) {
         ap->max_expansions > DPSO_ASTAR_MAX_EXPANSIONS || ap->inflate_r2 > 1024)
         return DPSO_ERR_RANGE;
     return DPSO_OK;
+}
+
+// The warp pass packs (f, h, voxel) into 22 + 18 + 24 bits: every voxel index
+// below 2^24, every heuristic (squared voxel distance) below 2^18, and every
+// f = g + h below 2^22, where g <= (max_expansions + 2) x the largest step.
+bool warp_pass_fits(const dpso_astar_params* ap) {
+    const long long nv = static_cast<long long>(ap->dims[0]) * ap->dims[1] * ap->dims[2];
+    long long hmax = 0;
+    for (int k = 0; k < 3; ++k) hmax += static_cast<long long>(ap->dims[k] - 1) * (ap->dims[k] - 1);
+    const long long gmax = (static_cast<long long>(ap->max_expansions) + 2) *
+                           (static_cast<long long>(ap->weights[0]) + ap->weights[1] + ap->weights[2]);
+    return nv < (1ll << 24) && hmax < (1ll << 18) && gmax + hmax < (1ll << 22);
+}
+
+cudaError_t run_warp_pass(const WarpArgs& W, cudaStream_t st) {
+    int dev = 0, sms = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int smem = kWarpsPerBlock * (kWarpOpen + kWarpSlots) * static_cast<int>(sizeof(unsigned long long));
+    if (e == cudaSuccess)
+        e = cudaFuncSetAttribute(astar_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    const int blocks = std::max(1, std::min(sms, (W.npairs + kWarpsPerBlock - 1) / kWarpsPerBlock));
+    astar_warp_kernel<<<blocks, 32 * kWarpsPerBlock, smem, st>>>(W);
+    return cudaGetLastError();
 }
 
 AstarGrid grid_of(const dpso_astar_params* ap) {
@@ -443,6 +668,7 @@ int dpso_cost_matrix_astar(const double* xyz_dev, int32_t n, const uint8_t* occ_
     for (int i = 0; i < n; ++i)
         for (int j = i + 1; j < n; ++j) pairs.push_back(make_int2(i, j));
     int *vox = nullptr, *retry = nullptr, *err = nullptr, *comp = nullptr;
+    unsigned* queue = nullptr;
     int2* dpairs = nullptr;
     const long long nv = static_cast<long long>(ap->dims[0]) * ap->dims[1] * ap->dims[2];
     auto cleanup = [&](int code) {
@@ -451,6 +677,7 @@ int dpso_cost_matrix_astar(const double* xyz_dev, int32_t n, const uint8_t* occ_
         cudaFreeAsync(retry, s);
         cudaFreeAsync(err, s);
         cudaFreeAsync(dpairs, s);
+        cudaFreeAsync(queue, s);
         cudaStreamSynchronize(s);
         return code;
     };
@@ -496,14 +723,43 @@ int dpso_cost_matrix_astar(const double* xyz_dev, int32_t n, const uint8_t* occ_
     A.n = n;
     A.err = err;
     constexpr size_t kBudget = size_t(4) << 30;  // scratch bytes per pass
-    // pass 1: every pair, room for a short search
-    const int e1 = std::min(kPass1Expansions, ap->max_expansions);
-    A.max_exp = e1;
-    A.final_pass = e1 == ap->max_expansions;
-    A.heap_cap = 26 * e1 + 1;
-    A.map_bits = map_bits_for(A.heap_cap);
     A.retry = retry;
-    if (e == cudaSuccess && np > 0) e = run_pass(A, dpairs, static_cast<int>(np), kBudget, s);
+    if (warp_pass_fits(ap)) {
+        // pass 1: every pair, one warp per search in shared memory, the full
+        // cap; searches that outgrow the warp's map or open array are retried
+        WarpArgs W{};
+        W.gr = gr;
+        W.occ = occ_dev;
+        W.vox = vox;
+        W.comp = comp;
+        W.pairs = dpairs;
+        W.npairs = static_cast<int>(np);
+        W.a1 = ap->weights[0];
+        W.a2 = ap->weights[1];
+        W.a3 = ap->weights[2];
+        W.unit_mm = ap->unit_mm;
+        W.blocked_cost = ap->blocked_cost;
+        W.max_exp = ap->max_expansions;
+        W.C = C_dev;
+        W.n = n;
+        W.retry = retry;
+        W.err = err;
+        A.final_pass = false;
+        if (e == cudaSuccess && np > 0) {
+            e = cudaMallocAsync(&queue, sizeof(unsigned), s);
+            if (e == cudaSuccess) e = cudaMemsetAsync(queue, 0, sizeof(unsigned), s);
+            W.queue = queue;
+            if (e == cudaSuccess) e = run_warp_pass(W, s);
+        }
+    } else {
+        // pass 1: every pair, room for a short search
+        const int e1 = std::min(kPass1Expansions, ap->max_expansions);
+        A.max_exp = e1;
+        A.final_pass = e1 == ap->max_expansions;
+        A.heap_cap = 26 * e1 + 1;
+        A.map_bits = map_bits_for(A.heap_cap);
+        if (e == cudaSuccess && np > 0) e = run_pass(A, dpairs, static_cast<int>(np), kBudget, s);
+    }
     // pass 2: the pairs that need more room, searched again from the start
     std::vector<int> flags(static_cast<size_t>(np));
     if (e == cudaSuccess && np > 0 && !A.final_pass) {

@@ -103,3 +103,33 @@ def test_astar_rejects_bad_parameters():
         with pytest.raises(dpso.DpsoError) as e:
             dpso.dpso_cost_matrix_astar(xyz, 2, occ, ap, C)
         assert e.value.status == status
+
+
+def test_search_outgrowing_the_warp_pass_bitwise():
+    """A wall with one gap at its far end: the search between the two sides
+    floods about 1960 voxels, more than the one-warp pass keeps in shared
+    memory, so it is searched again by the thread pass; the other pairs stay
+    in the warp pass."""
+    dims = (64, 64, 1)
+    boxes = [(32.0, 0.0, 0.0, 33.0, 62.0, 1.0)]
+    xyz = np.array([[10.5, 5.5, 0.5], [50.5, 5.5, 0.5], [5.5, 60.5, 0.5], [60.5, 30.5, 0.5],
+                    [20.5, 40.5, 0.5], [40.5, 63.5, 0.5]])
+    C = _astar_both(xyz, boxes, (0, 0, 0), 1.0, dims, blocked=999)
+    assert C[0, 1] == 77000 and (C != 999).all()
+
+
+def test_large_weights_take_the_thread_pass_bitwise():
+    """Step weights of about 1000 make f too wide for the warp pass's packed
+    keys; the thread pass then takes every pair (256 expansions, then the cap)."""
+    inst = inputs.random_instance(30, 5, 321, extent=10.0)
+    origin, dims = inputs.voxel_grid(inst, 0.5)
+    _astar_both(inst.xyz, inst.boxes, origin, 0.5, dims, r2=1, weights=(1000, 999, 998),
+                unit_mm=1, blocked=10 ** 8)
+
+
+def test_bridge_grid_bitwise():
+    """Viewpoints of the bridge workload on its 0.5 m grid with its boxes."""
+    inst = inputs.bridge()
+    sub = inst.xyz[::33]  # 61 viewpoints
+    origin, dims = inputs.voxel_grid(inst, 0.5)
+    _astar_both(sub, inst.boxes, origin, 0.5, dims, r2=inputs.inflate_r2(0.5, 0.5))

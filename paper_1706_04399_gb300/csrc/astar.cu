@@ -286,7 +286,8 @@ __global__ void astar_pairs_kernel(AstarArgs A) {
 // neighbour's test reads only its own slot), and the pop order depends only
 // on the set of keys, so the result is the sequential search's.  A search
 // that would outgrow the map or the open array is left to the global pass
-// (retry flag).  Host-checked bounds keep f < 2^22, h < 2^18, voxel < 2^24.
+// (retry flag).  Host-checked bounds keep f < 2^22, h < 2^18 and every grid
+// dimension at most 256.
 constexpr int kWarpSlots = 2048;         // map slots per warp
 constexpr int kWarpOpen = 2048;          // open entries per warp
 constexpr int kWarpDistinct = 1900;      // inserts before a search hands over
@@ -312,10 +313,19 @@ struct WarpArgs {
     int* err;
 };
 
+// Voxels in the warp pass are named by packed coordinates x | y << 8 | z << 16
+// (every grid dimension at most 256), which order like the voxel index
+// (z ny + y) nx + x, so keys need no division to give back coordinates.
+__device__ __forceinline__ int pack_xyz(int x, int y, int z) { return x | (y << 8) | (z << 16); }
+
+// Warp-wide minimum of a 64-bit key: the minimum of the high words, then of
+// the low words among the lanes holding it.
 __device__ __forceinline__ unsigned long long warp_min_key(unsigned long long v) {
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v = min(v, __shfl_xor_sync(0xffffffffu, v, o));
-    return v;
+    const unsigned hi = static_cast<unsigned>(v >> 32);
+    const unsigned mhi = __reduce_min_sync(0xffffffffu, hi);
+    const unsigned lo = hi == mhi ? static_cast<unsigned>(v) : 0xffffffffu;
+    const unsigned mlo = __reduce_min_sync(0xffffffffu, lo);
+    return (static_cast<unsigned long long>(mhi) << 32) | mlo;
 }
 
 __global__ void __launch_bounds__(32 * kWarpsPerBlock) astar_warp_kernel(WarpArgs A) {
@@ -329,7 +339,9 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) astar_warp_kernel(WarpArg
     const int d = lane < 13 ? lane : lane + 1;
     const int ddx = d % 3 - 1, ddy = (d / 3) % 3 - 1, ddz = d / 9 - 1;
     const int step = A.a1 * ddx * ddx + A.a2 * ddy * ddy + A.a3 * ddz * ddz;
-    auto slot0 = [](int v) { return (static_cast<unsigned>(v) * 2654435761u) >> 21; };  // 11 bits
+    auto slot0 = [](int c) { return (static_cast<unsigned>(c) * 2654435761u) >> 21; };  // 11 bits
+    auto cw = [](unsigned long long e) { return static_cast<int>((e >> 32) & (kClosed - 1)); };
+    constexpr unsigned long long kClosedBit = static_cast<unsigned long long>(kClosed) << 32;
     for (;;) {
         int k = 0;
         if (lane == 0) k = static_cast<int>(atomicAdd(A.queue, 1u));
@@ -343,49 +355,52 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) astar_warp_kernel(WarpArg
             for (int i = lane; i < kWarpSlots; i += 32) map[i] = kEmptySlot;
             const int tx = t % nx, ty = (t / nx) % ny, tz = t / nxy;
             const int sx = s % nx, sy = (s / nx) % ny, sz = s / nxy;
+            const int tc = pack_xyz(tx, ty, tz), sc = pack_xyz(sx, sy, sz);
             const int h0 = (sx - tx) * (sx - tx) + (sy - ty) * (sy - ty) + (sz - tz) * (sz - tz);
             __syncwarp();
             if (lane == 0) {
-                map[slot0(s)] = static_cast<unsigned long long>(s) << 32;  // g = 0
+                map[slot0(sc)] = static_cast<unsigned long long>(sc) << 32;  // g = 0
                 open[0] = (static_cast<unsigned long long>(h0) << 42) |
-                          (static_cast<unsigned long long>(h0) << 24) | static_cast<unsigned>(s);
+                          (static_cast<unsigned long long>(h0) << 24) | static_cast<unsigned>(sc);
             }
             int len = 1, distinct = 1, expanded = 0;
             __syncwarp();
             for (;;) {
-                // pop the smallest (f, h, voxel)
+                // pop the smallest (f, h, voxel); four independent loads per round
                 unsigned long long mine = ~0ull;
                 int at = -1;
-                for (int i = lane; i < len; i += 32) {
-                    const unsigned long long key = open[i];
-                    if (key < mine) {
-                        mine = key;
-                        at = i;
-                    }
+                for (int i = lane; i < len; i += 128) {
+                    const unsigned long long k0 = open[i];
+                    const unsigned long long k1 = i + 32 < len ? open[i + 32] : ~0ull;
+                    const unsigned long long k2 = i + 64 < len ? open[i + 64] : ~0ull;
+                    const unsigned long long k3 = i + 96 < len ? open[i + 96] : ~0ull;
+                    if (k0 < mine) { mine = k0; at = i; }
+                    if (k1 < mine) { mine = k1; at = i + 32; }
+                    if (k2 < mine) { mine = k2; at = i + 64; }
+                    if (k3 < mine) { mine = k3; at = i + 96; }
                 }
                 const unsigned long long top = warp_min_key(mine);
                 if (top == ~0ull) break;  // the open list is exhausted
                 if (mine == top) open[at] = ~0ull;
-                const int v = static_cast<int>(top & 0xffffffu);
+                const int c = static_cast<int>(top & 0xffffffu);
                 const int h = static_cast<int>((top >> 24) & 0x3ffffu);
                 const int g = static_cast<int>(top >> 42) - h;
                 // its slot exists (inserted when it was pushed); the probe is
                 // bounded all the same, and a miss hands the pair over
-                unsigned sv = slot0(v);
+                unsigned sv = slot0(c);
                 unsigned long long e = map[sv];
-                for (int probe = 1; probe < kWarpSlots &&
-                                    static_cast<int>((e >> 32) & (kClosed - 1)) != v; ++probe) {
+                for (int probe = 1; probe < kWarpSlots && cw(e) != c; ++probe) {
                     sv = (sv + 1) & (kWarpSlots - 1);
                     e = map[sv];
                 }
                 __syncwarp();
-                if (static_cast<int>((e >> 32) & (kClosed - 1)) != v) {
+                if (cw(e) != c) {
                     handover = true;
                     break;
                 }
-                if (e & (static_cast<unsigned long long>(kClosed) << 32)) continue;  // stale entry
-                if (lane == 0) map[sv] = e | (static_cast<unsigned long long>(kClosed) << 32);
-                if (v == t) {
+                if (e & kClosedBit) continue;  // stale entry
+                if (lane == 0) map[sv] = e | kClosedBit;
+                if (c == tc) {
                     result = g;
                     break;
                 }
@@ -395,48 +410,44 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) astar_warp_kernel(WarpArg
                     handover = true;
                     break;
                 }
-                const int x = v % nx, y = (v / nx) % ny, z = v / nxy;
-                const int xx = x + ddx, yy = y + ddy, zz = z + ddz;
+                const int xx = (c & 0xff) + ddx, yy = ((c >> 8) & 0xff) + ddy, zz = (c >> 16) + ddz;
                 bool push = false, inserted = false, lost = false;
                 unsigned long long key = 0;
-                if (lane < 26 && xx >= 0 && yy >= 0 && zz >= 0 && xx < nx && yy < ny && zz < nz) {
-                    const int u = (zz * ny + yy) * nx + xx;
-                    if (!__ldg(A.occ + u)) {
-                        const int gu = g + step;
-                        const unsigned long long want = (static_cast<unsigned long long>(u) << 32) |
-                                                        static_cast<unsigned>(gu);
-                        unsigned su = slot0(u);
-                        // fewer than kWarpSlots voxels are ever inserted, so an
-                        // empty slot ends the probe within kWarpSlots steps
-                        lost = true;
-                        for (int probe = 0; probe < kWarpSlots; ++probe) {
-                            unsigned long long cur = map[su];
+                if (lane < 26 && xx >= 0 && yy >= 0 && zz >= 0 && xx < nx && yy < ny && zz < nz &&
+                    !__ldg(A.occ + (zz * ny + yy) * nx + xx)) {
+                    const int u = pack_xyz(xx, yy, zz);
+                    const int gu = g + step;
+                    const unsigned long long want =
+                        (static_cast<unsigned long long>(u) << 32) | static_cast<unsigned>(gu);
+                    unsigned su = slot0(u);
+                    // fewer than kWarpSlots voxels are ever inserted, so an
+                    // empty slot ends the probe within kWarpSlots steps
+                    lost = true;
+                    for (int probe = 0; probe < kWarpSlots; ++probe) {
+                        unsigned long long cur = map[su];
+                        if (cur == kEmptySlot) {
+                            cur = atomicCAS(map + su, kEmptySlot, want);
                             if (cur == kEmptySlot) {
-                                cur = atomicCAS(map + su, kEmptySlot, want);
-                                if (cur == kEmptySlot) {
-                                    inserted = push = true;
-                                    lost = false;
-                                    break;
-                                }
-                            }
-                            if (static_cast<int>((cur >> 32) & (kClosed - 1)) == u) {
-                                if (!(cur & (static_cast<unsigned long long>(kClosed) << 32)) &&
-                                    gu < static_cast<int>(cur & 0xffffffffu)) {
-                                    map[su] = want;
-                                    push = true;
-                                }
+                                inserted = push = true;
                                 lost = false;
                                 break;
                             }
-                            su = (su + 1) & (kWarpSlots - 1);
                         }
-                        if (push) {
-                            const int hu = (xx - tx) * (xx - tx) + (yy - ty) * (yy - ty) +
-                                           (zz - tz) * (zz - tz);
-                            key = (static_cast<unsigned long long>(gu + hu) << 42) |
-                                  (static_cast<unsigned long long>(hu) << 24) |
-                                  static_cast<unsigned>(u);
+                        if (cw(cur) == u) {
+                            if (!(cur & kClosedBit) && gu < static_cast<int>(cur & 0xffffffffu)) {
+                                map[su] = want;
+                                push = true;
+                            }
+                            lost = false;
+                            break;
                         }
+                        su = (su + 1) & (kWarpSlots - 1);
+                    }
+                    if (push) {
+                        const int hu =
+                            (xx - tx) * (xx - tx) + (yy - ty) * (yy - ty) + (zz - tz) * (zz - tz);
+                        key = (static_cast<unsigned long long>(gu + hu) << 42) |
+                              (static_cast<unsigned long long>(hu) << 24) | static_cast<unsigned>(u);
                     }
                 }
                 if (__any_sync(0xffffffffu, lost)) {  // cannot happen (see above)
@@ -454,13 +465,13 @@ __global__ void __launch_bounds__(32 * kWarpsPerBlock) astar_warp_kernel(WarpArg
             if (handover) {
                 A.retry[k] = 1;
             } else {
-                long long c = result < 0 ? A.blocked_cost : result * A.unit_mm;
-                if (c > DPSO_COST_MAX) {
+                long long cost = result < 0 ? A.blocked_cost : result * A.unit_mm;
+                if (cost > DPSO_COST_MAX) {
                     atomicOr(A.err, 2);
-                    c = DPSO_COST_MAX;
+                    cost = DPSO_COST_MAX;
                 }
-                A.C[static_cast<size_t>(pr.x) * A.n + pr.y] = static_cast<int>(c);
-                A.C[static_cast<size_t>(pr.y) * A.n + pr.x] = static_cast<int>(c);
+                A.C[static_cast<size_t>(pr.x) * A.n + pr.y] = static_cast<int>(cost);
+                A.C[static_cast<size_t>(pr.y) * A.n + pr.x] = static_cast<int>(cost);
             }
         }
         __syncwarp();
@@ -549,16 +560,17 @@ int check_params(const dpso_astar_params* ap) {
     return DPSO_OK;
 }
 
-// The warp pass packs (f, h, voxel) into 22 + 18 + 24 bits: every voxel index
-// below 2^24, every heuristic (squared voxel distance) below 2^18, and every
-// f = g + h below 2^22, where g <= (max_expansions + 2) x the largest step.
+// The warp pass packs (f, h, voxel) into 22 + 18 + 24 bits: every grid
+// dimension at most 256 (8 bits per packed coordinate), every heuristic
+// (squared voxel distance) below 2^18, and every f = g + h below 2^22, where
+// g <= (max_expansions + 2) x the largest step.
 bool warp_pass_fits(const dpso_astar_params* ap) {
-    const long long nv = static_cast<long long>(ap->dims[0]) * ap->dims[1] * ap->dims[2];
     long long hmax = 0;
     for (int k = 0; k < 3; ++k) hmax += static_cast<long long>(ap->dims[k] - 1) * (ap->dims[k] - 1);
     const long long gmax = (static_cast<long long>(ap->max_expansions) + 2) *
                            (static_cast<long long>(ap->weights[0]) + ap->weights[1] + ap->weights[2]);
-    return nv < (1ll << 24) && hmax < (1ll << 18) && gmax + hmax < (1ll << 22);
+    return ap->dims[0] <= 256 && ap->dims[1] <= 256 && ap->dims[2] <= 256 && hmax < (1ll << 18) &&
+           gmax + hmax < (1ll << 22);
 }
 
 cudaError_t run_warp_pass(const WarpArgs& W, cudaStream_t st) {

@@ -133,3 +133,14 @@ def test_bridge_grid_bitwise():
     sub = inst.xyz[::33]  # 61 viewpoints
     origin, dims = inputs.voxel_grid(inst, 0.5)
     _astar_both(sub, inst.boxes, origin, 0.5, dims, r2=inputs.inflate_r2(0.5, 0.5))
+
+
+def test_grid_wider_than_256_takes_the_thread_pass_bitwise():
+    """A grid dimension above 256 does not fit the warp pass's packed voxel
+    coordinates; the thread pass takes every pair."""
+    dims = (300, 4, 3)
+    boxes = [(100.0, 0.0, 0.0, 101.0, 3.0, 3.0), (200.0, 1.0, 0.0, 201.0, 4.0, 3.0)]
+    rng = np.random.default_rng(8)
+    xyz = np.column_stack([rng.uniform(0, 300, 12), rng.uniform(0, 4, 12), rng.uniform(0, 3, 12)])
+    C = _astar_both(xyz, boxes, (0, 0, 0), 1.0, dims, blocked=777)
+    assert (C == 777).sum() < C.size - 12

@@ -17,6 +17,10 @@ e2e     the same metric through dpso_plan from pinned host buffers: copies in,
 roofline  the 2-opt kernel: 8 bytes of C per candidate pair (two int32 entries)
         over its CUDA-event time, against the L2 read bandwidth measured in
         this run (the cost matrix is L2-resident; rows are staged from L2).
+fitness_roofline  the tour-fitness kernel (Eq. min) over the swarm's tours:
+        4 n bytes of C gathered per tour over its CUDA-event time, against the
+        random 4-byte gather rate from an L2-resident buffer measured in this
+        run.
 
 `--impl reference` times the CPU oracle on a bounded sample of the workload.
 """
@@ -140,20 +144,24 @@ def run_reference(args):
 # ------------------------------------------------------------------ GPU helpers
 
 class ClockSampler:
-    """nvidia-smi clock / throttle samples every 200 ms while running."""
+    """nvidia-smi clock / throttle samples every 50 ms while running.  When
+    start() / stop() mark a window, summary() keeps the samples whose
+    timestamps fall inside it (the process is started earlier, so its start-up
+    does not eat a short timed region)."""
 
-    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
+    FIELDS = ("timestamp,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.hw_slowdown,"
               "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
               "clocks_event_reasons.sw_power_cap,utilization.gpu")
 
     def __init__(self, index: str | None):
         self.index = index
         self.proc = None
+        self.window = None
         self.out = os.path.join("/tmp", f"dpso_clocks_{os.getpid()}.csv")
 
     def __enter__(self):
         cmd = ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
-               "-lms", "200"]
+               "-lms", "50"]
         if self.index is not None:
             cmd += ["-i", self.index]
         try:
@@ -162,6 +170,13 @@ class ClockSampler:
         except OSError:
             self.proc = None
         return self
+
+    def start(self):
+        self.window = [time.time(), None]
+
+    def stop(self):
+        if self.window:
+            self.window[1] = time.time()
 
     def __exit__(self, *exc):
         if self.proc is not None:
@@ -172,6 +187,14 @@ class ClockSampler:
                 self.proc.kill()
             self.fh.close()
 
+    @staticmethod
+    def _stamp(text):
+        import datetime
+        try:
+            return datetime.datetime.strptime(text, "%Y/%m/%d %H:%M:%S.%f").timestamp()
+        except ValueError:
+            return None
+
     def summary(self):
         if self.proc is None or not os.path.exists(self.out):
             return None
@@ -179,11 +202,19 @@ class ClockSampler:
         with open(self.out) as fh:
             for line in fh:
                 parts = [p.strip() for p in line.split(",")]
-                if len(parts) >= 8:
+                if len(parts) >= 9:
                     rows.append(parts)
         os.unlink(self.out)
+        total = len(rows)
+        if self.window and self.window[1] is not None:
+            lo, hi = self.window[0] - 0.05, self.window[1] + 0.05
+            stamped = [(self._stamp(r[0]), r) for r in rows]
+            if all(t is not None for t, _ in stamped):
+                rows = [r for t, r in stamped if lo <= t <= hi]
+        rows = [r[1:] for r in rows]
         if not rows:
-            return None
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0,
+                    "samples_under_load": 0, "samples_all": total}
 
         def num(v):
             try:
@@ -199,7 +230,9 @@ class ClockSampler:
         return {"sm_mhz": statistics.median(loaded) if loaded else None,
                 "sm_max_mhz": max(num(r[1]) or 0 for r in rows),
                 "reasons": reasons, "samples": len(rows),
-                "samples_under_load": sum(1 for u in util if u is not None and u > 50)}
+                "samples_under_load": sum(1 for u in util if u is not None and u > 50),
+                "samples_all": total,
+                "window": "timed region" if self.window else "whole run"}
 
 
 def gpu_index_for_smi(local_rank: int) -> str | None:
@@ -232,6 +265,38 @@ def two_opt_traffic(workload_name: str):
     if rec.get("kernel_source_sha256") != digest or rec.get("workload") != workload_name:
         return None
     return rec.get("dram_bytes_per_launch")
+
+
+def fitness_roofline(dpso, C, n: int, X, stream, reps: int = 20) -> dict:
+    """Times dpso_fitness over the tours X (count x n uint16, host) on `stream`:
+    mean CUDA-event duration of `reps` back-to-back launches after three warm-up
+    launches (the cost matrix stays L2-resident, as in a generation), against
+    the L2 random-gather rate measured by dpso_probe_l2_gather_gbs on a buffer
+    of the cost matrix's size (at least 8 MiB)."""
+    import numpy as np
+    import torch
+    count = X.shape[0]
+    T = torch.from_numpy(np.ascontiguousarray(X).view(np.int16)).cuda()
+    out = torch.empty(count, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        dpso.dpso_fitness(C, n, T, count, out, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        dpso.dpso_fitness(C, n, T, count, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    probe_bytes = max(8 << 20, 4 * n * n)
+    peak = dpso.dpso_probe_l2_gather_gbs(probe_bytes, 64, stream)
+    algo = 4 * n * count
+    achieved = algo / (ms / 1e3) / 1e9
+    return {"kernel": "fitness_kernel", "bound": "l2_gather", "bytes_per_launch": algo,
+            "tours": count, "ms_per_launch": ms, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak if peak else None, "traffic": None,
+            "peak_source": f"random 4-byte gathers from an L2-resident {probe_bytes >> 20} MiB "
+                           "buffer measured in this run by dpso_probe_l2_gather_gbs "
+                           "(best of 5)"}
 
 
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
@@ -277,6 +342,8 @@ def gpu_line(args):
     flags = dpso.FLAGS_ALL | (dpso.FLAG_NODE_SWAP if node_swap else 0)
     params = dpso.default_params(swarm=S, flags=flags)
     sw = dpso.Swarm(C, n, inst.tags, params, seed, stream)
+    sampler = ClockSampler(gpu_index_for_smi(local))
+    sampler.__enter__()            # sampling from here; the timed window is marked below
     sw.set_timing(True)
     sw.step(args.warmup, stream)
     torch.cuda.synchronize()
@@ -289,15 +356,16 @@ def gpu_line(args):
     if dist:
         dist.barrier()
     torch.cuda.synchronize()
-    sampler = ClockSampler(gpu_index_for_smi(local))
     wall0 = time.perf_counter()
-    with sampler:
-        for k in range(args.steps):
-            flush.zero_()                      # evict the L2 between generations
-            evs[k][0].record(stream)
-            sw.step(1, stream)
-            evs[k][1].record(stream)
-        torch.cuda.synchronize()
+    sampler.start()
+    for k in range(args.steps):
+        flush.zero_()                      # evict the L2 between generations
+        evs[k][0].record(stream)
+        sw.step(1, stream)
+        evs[k][1].record(stream)
+    torch.cuda.synchronize()
+    sampler.stop()
+    sampler.__exit__(None, None, None)
     wall = time.perf_counter() - wall0
     if dist:
         dist.barrier()
@@ -336,6 +404,7 @@ def gpu_line(args):
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
             "frac_of_hbm_peak": achieved / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
         }
+        fit_roof = fitness_roofline(dpso, C, n, sw.state()["X"], stream)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cs, cg = cpu_sample_shape(n, node_swap)
@@ -382,7 +451,7 @@ def gpu_line(args):
             "two_opt_moves_applied": moves, "two_opt_pairs": pairs,
             "two_opt_pairs_evaluated": evaluated,
             "phase_ms": phases, "wall_s": wall,
-            "roofline": roofline, "cpu_baseline": cpu, "e2e": e2e,
+            "roofline": roofline, "fitness_roofline": fit_roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": sampler.summary(),
             "gbest_cost_mm": st1["gbest_cost"],
         }

@@ -466,6 +466,17 @@ int dpso_philox_draws(uint64_t seed, uint32_t phase, uint32_t iteration, uint32_
  */
 int dpso_probe_l2_read_gbs(size_t bytes, int32_t reps, double *gbs, void *stream);
 
+/*
+ * Measurement aid (no counterpart in the paper): the rate, in GB/s of 4-byte
+ * words delivered, of independent random 4-byte gathers from an L2-resident
+ * device buffer of `bytes` (4096 .. 2^33; allocated and freed by the call):
+ * the access shape of a tour-fitness evaluation, Eq. (min), where each term
+ * C[x_k][x_k+1] is one such gather.  Every thread of 8 CTAs per SM issues
+ * `reps` rounds of eight gathers; best of five timed runs with CUDA events on
+ * `stream`.  Synchronises `stream`.
+ */
+int dpso_probe_l2_gather_gbs(size_t bytes, int32_t reps, double *gbs, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

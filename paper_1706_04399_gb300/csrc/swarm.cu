@@ -30,9 +30,18 @@ __device__ __forceinline__ unsigned long long warp_sum_u(unsigned long long v) {
 __device__ __forceinline__ long long tour_cost_warp(const int* __restrict__ C, int ldc, int n,
                                                     const uint16_t* x, int lane) {
     long long f = 0;
-    for (int i = lane; i < n; i += 32) {
-        const int a = x[i], b = x[i + 1 == n ? 0 : i + 1];
-        f += C[(size_t)a * ldc + b];
+    // eight positions per lane per round, their gathers issued together
+    for (int base = 0; base < n; base += 256) {
+        int a[8], b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = base + lane + 32 * k;
+            a[k] = i < n ? x[i] : 0;
+            b[k] = i < n ? x[i + 1 == n ? 0 : i + 1] : 0;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (base + lane + 32 * k < n) f += C[(size_t)a[k] * ldc + b[k]];
     }
     return warp_sum(f);
 }
@@ -46,9 +55,20 @@ __global__ void fitness_kernel(const int* __restrict__ C, int ldc, int n,
     if (w >= count) return;
     const uint16_t* x = tours + (size_t)w * ldt;
     long long f = 0;
-    for (int i = lane; i < n; i += 32) {
-        const int a = x[i], b = x[i + 1 == n ? 0 : i + 1];
-        if (a < n && b < n) f += C[(size_t)a * ldc + b];
+    // A round covers 256 positions, eight per lane (lane, lane + 32, ...): the
+    // labels of all eight edges are read first, then the eight gathers from C
+    // are issued together, so every lane keeps eight L2 requests in flight.
+    for (int base = 0; base < n; base += 256) {
+        int a[8], b[8];
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const int i = base + lane + 32 * k;
+            a[k] = i < n ? x[i] : n;
+            b[k] = i < n ? x[i + 1 == n ? 0 : i + 1] : n;
+        }
+#pragma unroll
+        for (int k = 0; k < 8; ++k)
+            if (a[k] < n && b[k] < n) f += C[(size_t)a[k] * ldc + b[k]];
     }
     f = warp_sum(f);
     if (lane == 0) out[w] = f;

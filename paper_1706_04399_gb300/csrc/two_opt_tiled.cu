@@ -139,8 +139,14 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
     __shared__ unsigned int s_next[TPC];     // tiles taken in this pass (TG = 2)
     __shared__ int s_tile[TPC * TG * 2];     // a subgroup's next tile, by parity
     __shared__ int s_mode[TPC * TG];         // 1: the subgroup's tile is full
-    __shared__ int s_part[TPC], s_e0[TPC], s_e1[TPC];
-    __shared__ long long s_pf[TPC];
+    __shared__ int s_part[TPC], s_e0[TPC], s_e1[TPC], s_p[TPC];
+    __shared__ long long s_pf[TPC], s_f[TPC];
+    // The tour's task descriptor, its running cost and the subgroups' counts of
+    // evaluated pairs live in shared memory rather than registers: they are
+    // read once per pass, tile or tour, and registers are what limits this
+    // kernel to 64 per thread.
+    __shared__ TwoOptTask s_task[TPC];
+    __shared__ unsigned long long s_evals[TPC * TG];
     // tile-arrival barrier per tile subgroup; a subgroup whose tile copy did
     // not complete sets its own abort flag (read by its own threads after its
     // barrier, by the whole tour after a tour barrier)
@@ -177,9 +183,15 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         group_sync<TPC>(grp);
         const int g = s_part[grp];
         if (g >= b.total) break;
-        const int prob = find_inst(b.off, b.nprob, g);
-        const TwoOptTask a = b.tasks[prob];
-        const int p = a.order ? a.order[g - b.off[prob]] : g - b.off[prob];
+        if (tid == 0) {
+            const int prob = find_inst(b.off, b.nprob, g);
+            s_task[grp] = b.tasks[prob];
+            const int* order = b.tasks[prob].order;
+            s_p[grp] = order ? order[g - b.off[prob]] : g - b.off[prob];
+        }
+        group_sync<TPC>(grp);
+        const TwoOptTask& a = s_task[grp];
+        const int p = s_p[grp];
         if (a.gate && *a.gate == 0) {  // this problem does not exchange edges now
             group_sync<TPC>(grp);
             continue;
@@ -191,9 +203,6 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         const int xs16 = (rec2 + n + 4) * 4;    // uint16 index of x_0
         // u64 index of the row cache, after the tour (n + 1 uint16, padded)
         const int rk64 = (xs16 + (n + 1 + 7) / 8 * 8 + 3) / 4;
-        const int* __restrict__ C = a.C;
-        const int ldc = a.ldc;
-        const long long npairs = static_cast<long long>(n) * (n - 3) / 2;
         const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
         const int guard = 1000 + 100 * n;
 
@@ -206,7 +215,6 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         // still waits for that one arrival).  Offsets into the shifted copies
         // fit 32 bits (4 n ldq words < 2^30).
         constexpr int kPerWarp = (kStaged + WSG - 1) / WSG;
-        const char* const cs0 = reinterpret_cast<const char*>(a.Cs);
         const unsigned tile_s = smem_addr(smi + half * buf_words);
         const unsigned row_bytes = static_cast<unsigned>(ldq) * 4u;
         auto stage = [&](int I, int count) {
@@ -217,7 +225,8 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
             if (lane < kPerWarp && r < count) {
                 const unsigned k = (r >> 3) & 3;
                 const unsigned off = (k * static_cast<unsigned>(n) + smu[xs16 + I + r]) * row_bytes;
-                bulk_row(tile_s + r * row_bytes, cs0 + off, row_bytes, mbar);
+                bulk_row(tile_s + r * row_bytes, reinterpret_cast<const char*>(a.Cs) + off,
+                         row_bytes, mbar);
             }
         };
         // Every thread waits for the tile's bytes, at most ~2 s of clock; a
@@ -239,16 +248,19 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
             phase ^= 1u;
         };
 
-        uint16_t* tour = a.tours + static_cast<size_t>(p) * a.ldt;
-        for (int i = tid; i < n; i += GT) smu[xs16 + i] = tour[i];
-        if (tid == 0) smu[xs16 + n] = tour[0];
+        {
+            const uint16_t* tour = a.tours + static_cast<size_t>(p) * a.ldt;
+            for (int i = tid; i < n; i += GT) smu[xs16 + i] = tour[i];
+            if (tid == 0) smu[xs16 + n] = tour[0];
+        }
         group_sync<TPC>(grp);
         for (int c = tid; c < n; c += GT) {
             const int u = smu[xs16 + c], v = smu[xs16 + c + 1];
-            smi2[rec2 + c] = make_int2(4 * v, -C[static_cast<size_t>(u) * ldc + v]);
+            smi2[rec2 + c] = make_int2(4 * v, -a.C[static_cast<size_t>(u) * a.ldc + v]);
         }
         if (tid < 4) smi2[rec2 + n + tid] = make_int2(0, kPadCost);
-        long long f = a.cost[p];
+        if (tid == 0) s_f[grp] = a.cost[p];
+        if (wsg == 0 && lane == 0) s_evals[sg] = 0;
         int moves = 0, passes = 0;
         group_sync<TPC>(grp);
 
@@ -259,7 +271,6 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         // The warps of a tile fold their keys into it with shared atomicMin.
         unsigned long long* const rowkey = reinterpret_cast<unsigned long long*>(smi) + rk64;
         int pa = -1, pb = -1;  // the previous move; pb < 0: evaluate every pair
-        unsigned long long evals = 0;  // pairs evaluated (lane 0 of a subgroup's warp 0)
         if (tid == 0) {
             s_best[grp] = ~0ull;
             s_next[grp] = 0;
@@ -338,7 +349,8 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                     const int E = min(cstart + 4 * ngroups, n);
                     int cnt = row_ok ? max(0, E - max(cstart, i + 2)) : 0;
                     cnt -= (i == 0 && E == n && cnt > 0) ? 1 : 0;
-                    evals += __reduce_add_sync(0xffffffffu, static_cast<unsigned>(cnt));
+                    const unsigned tc = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(cnt));
+                    if (lane == 0) s_evals[sg] += tc;
                 }
                 // first valid column of this lane's row (rows past n-3 have none)
                 const int lim = row_ok ? i + 2 : INT_MAX;
@@ -404,8 +416,10 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                 if (lane < 4 && j >= bi + 2 && j <= n - 1) {
                     const int xi = smu[xs16 + bi], xi1 = smu[xs16 + bi + 1];
                     const int xj = smu[xs16 + j], xj1 = smu[xs16 + j + 1];
-                    e0 = C[static_cast<size_t>(xi) * ldc + xj];
-                    e1 = C[static_cast<size_t>(xi1) * ldc + xj1];
+                    const int* C = a.C;
+                    const size_t ldc = static_cast<size_t>(a.ldc);
+                    e0 = C[xi * ldc + xj];
+                    e1 = C[xi1 * ldc + xj1];
                     match = e0 + e1 + smi2[rec2 + j].y + smi2[rec2 + bi].y == bd;
                 }
                 const unsigned mm = __ballot_sync(0xffffffffu, match);
@@ -441,27 +455,32 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
             for (int cc = bi + tid; cc <= bj; cc += GT)
                 smi2[rec2 + cc] = make_int2(4 * smu[xs16 + cc + 1],
                                             cc == bi ? -ei : (cc == bj ? -ej : smi2[rec2 + cc].y));
-            f += bd;
+            if (tid == 0) s_f[grp] += bd;
             ++moves;
             pa = bi;
             pb = bj;
             group_sync<TPC>(grp);
         }
 
-        if (wsg == 0 && lane == 0 && a.evals && evals) atomicAdd(a.evals, evals);
-        for (int i = tid; i < n; i += GT) tour[i] = smu[xs16 + i];
+        if (wsg == 0 && lane == 0 && a.evals && s_evals[sg]) atomicAdd(a.evals, s_evals[sg]);
+        {
+            uint16_t* tour = a.tours + static_cast<size_t>(p) * a.ldt;
+            for (int i = tid; i < n; i += GT) tour[i] = smu[xs16 + i];
+        }
         if (tid == 0) {
-            a.cost[p] = f;
+            a.cost[p] = s_f[grp];
             if (a.tour_passes) {
                 a.tour_passes[p] = static_cast<unsigned int>(passes);
                 a.tour_moves[p] = static_cast<unsigned int>(moves);
             } else {
+                const long long npairs = static_cast<long long>(n) * (n - 3) / 2;
                 atomicAdd(a.pairs, static_cast<unsigned long long>(passes) * npairs);
                 atomicAdd(a.moves, static_cast<unsigned long long>(moves));
             }
             s_pf[grp] = a.pbest ? a.pcost[p] : LLONG_MIN;
         }
         group_sync<TPC>(grp);
+        const long long f = s_f[grp];
         if (a.pbest && f < s_pf[grp]) {
             uint16_t* pb = a.pbest + static_cast<size_t>(p) * a.ldt;
             for (int i = tid; i < n; i += GT) pb[i] = smu[xs16 + i];
@@ -509,12 +528,13 @@ cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int tg, int num_sms, cuda
 
 }  // namespace
 
-// Resident CTAs per SM for a shape: shared memory (228 KB per SM, 1 KB
-// reserved per CTA) against registers (256-thread CTAs: 64 per thread at
-// R = 30, else 80; 512-thread CTAs: 64).
+// Resident CTAs per SM for a shape: shared memory (228 KB per SM; per CTA
+// 1 KB reserved by the system and under 1 KB of the kernel's static shared
+// variables) against registers (256-thread CTAs: 64 per thread at R = 30,
+// else 80; 512-thread CTAs: 64).
 int two_opt_tiled_ctas(int n, int rows, int tpc, int tg) {
     const int by_smem =
-        static_cast<int>((228 * 1024) / (group_bytes(n, rows, tg) * tpc + 1024));
+        static_cast<int>((228 * 1024) / (group_bytes(n, rows, tg) * tpc + 2048));
     return min(by_smem, tg == 2 ? 2 : (rows == 30 ? 4 : 3));
 }
 

@@ -133,6 +133,8 @@ def lib():
             "dpso_cost_matrix": (ctypes.c_int, [_vp, _i32, _vp, _i32,
                                                 ctypes.POINTER(dpso_cost_params), _vp, _vp]),
             "dpso_fitness": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
+            "dpso_probe_l2_gather_gbs": (ctypes.c_int, [ctypes.c_size_t, _i32,
+                                                        ctypes.POINTER(ctypes.c_double), _vp]),
             "dpso_two_opt": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p, _vp]),
             "dpso_default_astar_params": (None, [ctypes.POINTER(dpso_astar_params)]),
             "dpso_voxel_occupancy": (ctypes.c_int, [_vp, _i32, ctypes.POINTER(dpso_astar_params),
@@ -296,6 +298,14 @@ def dpso_probe_l2_read_gbs(nbytes: int = 24 << 20, reps: int = 40, stream=None) 
     out = ctypes.c_double(0.0)
     _check(lib().dpso_probe_l2_read_gbs(nbytes, reps, ctypes.byref(out), _stream(stream)),
            "dpso_probe_l2_read_gbs")
+    return out.value
+
+
+def dpso_probe_l2_gather_gbs(nbytes: int = 16 << 20, reps: int = 64, stream=None) -> float:
+    """Measured rate (GB/s of 4-byte words) of random gathers from an L2-resident buffer."""
+    out = ctypes.c_double(0.0)
+    _check(lib().dpso_probe_l2_gather_gbs(nbytes, reps, ctypes.byref(out), _stream(stream)),
+           "dpso_probe_l2_gather_gbs")
     return out.value
 
 

@@ -106,3 +106,26 @@ def test_oracle_sample_is_bounded_by_instance_size():
     assert bench.cpu_sample_shape(400, node_swap=True) == (16, 4)
     s, g = bench.cpu_sample_shape(1992)
     assert s * g <= 4
+
+
+def test_clock_samples_are_kept_only_inside_the_timed_window(tmp_path):
+    # samples before and after the marked window (a slow start-up, an idle
+    # tail) must not enter the reported clocks or throttle reasons
+    import datetime
+    cs = bench.ClockSampler(None)
+    cs.proc = object()                 # as if nvidia-smi had run
+    cs.out = str(tmp_path / "clocks.csv")
+    t = 1_800_000_000.0
+
+    def stamp(x):
+        return datetime.datetime.fromtimestamp(x).strftime("%Y/%m/%d %H:%M:%S.%f")[:-3]
+    rows = [(-1.0, 900, "Active"), (0.02, 2070, "Not Active"), (0.1, 2040, "Not Active"),
+            (2.0, 800, "Active")]
+    with open(cs.out, "w") as fh:
+        for dt, mhz, slow in rows:
+            fh.write(f"{stamp(t + dt)}, {mhz}, 2070, 900.0, {slow}, Not Active, Not Active, "
+                     "Not Active, 99\n")
+    cs.window = [t, t + 0.2]
+    got = cs.summary()
+    assert got["samples"] == 2 and got["samples_all"] == 4
+    assert got["sm_mhz"] == 2055.0 and got["reasons"] == []

@@ -252,51 +252,23 @@ def measured_peaks() -> dict:
         return {}
 
 
-def two_opt_traffic(workload_name: str):
-    """DRAM bytes per 2-opt launch from the committed ncu summary, if it was
-    taken from the current kernel source (else None)."""
-    src = os.path.join(ROOT, "paper_1706_04399_gb300", "csrc", "two_opt_tiled.cu")
-    path = os.path.join(ROOT, "profiles", "two_opt_dram_traffic.json")
+def dram_traffic(kernel: str, workload_name: str):
+    """DRAM bytes per launch of `kernel` on `workload_name` from the committed
+    ncu summary, if it was taken from the current kernel source (else None)."""
+    path = os.path.join(ROOT, "profiles", "dram_traffic.json")
     try:
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()
-        rec = json.load(open(path))
-    except (OSError, ValueError):
+        recs = json.load(open(path))["records"]
+    except (OSError, ValueError, KeyError):
         return None
-    if rec.get("kernel_source_sha256") != digest or rec.get("workload") != workload_name:
-        return None
-    return rec.get("dram_bytes_per_launch")
-
-
-def fitness_roofline(dpso, C, n: int, X, stream, reps: int = 20) -> dict:
-    """Times dpso_fitness over the tours X (count x n uint16, host) on `stream`:
-    mean CUDA-event duration of `reps` back-to-back launches after three warm-up
-    launches (the cost matrix stays L2-resident, as in a generation), against
-    the L2 random-gather rate measured by dpso_probe_l2_gather_gbs on a buffer
-    of the cost matrix's size (at least 8 MiB)."""
-    import numpy as np
-    import torch
-    count = X.shape[0]
-    T = torch.from_numpy(np.ascontiguousarray(X).view(np.int16)).cuda()
-    out = torch.empty(count, dtype=torch.int64, device="cuda")
-    for _ in range(3):
-        dpso.dpso_fitness(C, n, T, count, out, stream)
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(reps):
-        dpso.dpso_fitness(C, n, T, count, out, stream)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    ms = e0.elapsed_time(e1) / reps
-    probe_bytes = max(8 << 20, 4 * n * n)
-    peak = dpso.dpso_probe_l2_gather_gbs(probe_bytes, 64, stream)
-    algo = 4 * n * count
-    achieved = algo / (ms / 1e3) / 1e9
-    return {"kernel": "fitness_kernel", "bound": "l2_gather", "bytes_per_launch": algo,
-            "tours": count, "ms_per_launch": ms, "achieved": achieved, "peak": peak,
-            "unit": "GB/s", "frac": achieved / peak if peak else None, "traffic": None,
-            "peak_source": f"random 4-byte gathers from an L2-resident {probe_bytes >> 20} MiB "
-                           "buffer measured in this run by dpso_probe_l2_gather_gbs "
-                           "(best of 5)"}
+    for rec in recs:
+        if rec.get("kernel") != kernel or rec.get("workload") != workload_name:
+            continue
+        try:
+            digest = hashlib.sha256(open(os.path.join(ROOT, rec["source"]), "rb").read()).hexdigest()
+        except (OSError, KeyError):
+            return None
+        return rec.get("dram_bytes_per_launch") if rec.get("source_sha256") == digest else None
+    return None
 
 
 def max_over_ranks(value: float, dist=None, device="cpu") -> float:
@@ -390,7 +362,7 @@ def gpu_line(args):
         # bytes of the pairs the kernel evaluated (a pass skips the rows the
         # last move left unchanged), not of the pairs a plain scan would take
         achieved = bpp * evaluated / (two_ms / 1e3) / 1e9 if two_ms > 0 else 0.0
-        traffic = None if node_swap else two_opt_traffic(inst.name)
+        traffic = None if node_swap else dram_traffic("two_opt_tiled_kernel", inst.name)
         roofline = {
             "kernel": "node_swap_tiled_kernel" if node_swap else "two_opt_tiled_kernel",
             "bound": "l2", "bytes_per_pair": bpp, "pairs_evaluated": evaluated,
@@ -404,7 +376,7 @@ def gpu_line(args):
             "hbm_peak_gbs": peaks.get("hbm_gbs"),
             "frac_of_hbm_peak": achieved / peaks["hbm_gbs"] if peaks.get("hbm_gbs") else None,
         }
-        fit_roof = fitness_roofline(dpso, C, n, sw.state()["X"], stream)
+        fit_roof = fitness_roofline(dpso, C, n, sw.state()["X"], stream, inst.name)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
             cs, cg = cpu_sample_shape(n, node_swap)

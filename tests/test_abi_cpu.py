@@ -54,6 +54,12 @@ def test_argument_errors_need_no_device(libpath):
     assert L.dpso_init(ctypes.byref(h), 1, 10, None, ctypes.byref(bad), 1, None) == dpso.ERR_ARG
     big = dpso.default_params(swarm=70000)
     assert L.dpso_init(ctypes.byref(h), 1, 10, None, ctypes.byref(big), 1, None) == dpso.ERR_RANGE
+    # the probes check their arguments before touching a device
+    g = ctypes.c_double(0.0)
+    assert L.dpso_probe_l2_gather_gbs(1024, 4, ctypes.byref(g), None) == dpso.ERR_ARG
+    assert L.dpso_probe_l2_gather_gbs(8 << 20, 0, ctypes.byref(g), None) == dpso.ERR_ARG
+    assert L.dpso_probe_l2_gather_gbs(8 << 20, 4, None, None) == dpso.ERR_ARG
+    assert L.dpso_probe_l2_read_gbs(1024, 4, ctypes.byref(g), None) == dpso.ERR_ARG
     ok = dpso.default_params()
     assert L.dpso_init(ctypes.byref(h), 1, dpso.MAX_N + 1, None, ctypes.byref(ok), 1,
                        None) == dpso.ERR_RANGE

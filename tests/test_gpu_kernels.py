@@ -92,7 +92,7 @@ def test_cost_matrix_errors():
 
 # -------------------------------------------------------------------- fitness
 
-@pytest.mark.parametrize("n", [3, 31, 32, 33, 400, 1992])
+@pytest.mark.parametrize("n", [3, 31, 32, 33, 255, 256, 257, 400, 513, 1992])
 def test_fitness_bitwise(n):
     C_np = inputs.random_cost_matrix(n, n, hi=dpso.COST_MAX)
     tours = inputs.random_tours(n, 37, n + 1)
@@ -102,6 +102,34 @@ def test_fitness_bitwise(n):
     dpso.dpso_fitness(C, n, T, 37, out)
     got = out.cpu().numpy()
     assert np.array_equal(got, [oracle.fitness(C_np, t) for t in tours])
+
+
+def test_fitness_skips_labels_outside_the_tour_range():
+    # dpso_fitness's contract: an edge with a label outside [0, n) adds nothing
+    # (and never indexes C); the others add their cost as usual
+    n = 300
+    C_np = inputs.random_cost_matrix(n, 11)
+    tours = inputs.random_tours(n, 5, 12)
+    tours[1, 0] = n
+    tours[2, 299] = 65535
+    tours[3, 100:140] = n + 7
+    tours[4, :] = n
+    C = torch.from_numpy(C_np).to(DEV)
+    T = torch.from_numpy(tours.view(np.int16)).to(DEV)
+    out = torch.empty(5, dtype=torch.int64, device=DEV)
+    dpso.dpso_fitness(C, n, T, 5, out)
+    want = []
+    for t in tours.astype(np.int64):
+        nxt = np.roll(t, -1)
+        ok = (t < n) & (nxt < n)
+        want.append(int(C_np[t[ok], nxt[ok]].astype(np.int64).sum()))
+    assert np.array_equal(out.cpu().numpy(), want)
+    assert want[0] == oracle.fitness(C_np, tours[0])
+
+
+def test_gather_probe_reports_a_rate():
+    g = dpso.dpso_probe_l2_gather_gbs(8 << 20, 4)
+    assert 1.0 < g < 1e6
 
 
 # ---------------------------------------------------------------------- 2-opt

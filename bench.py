@@ -252,6 +252,39 @@ def measured_peaks() -> dict:
         return {}
 
 
+def fitness_roofline(dpso, C, n: int, X, stream, workload_name: str, reps: int = 20) -> dict:
+    """Times dpso_fitness over the tours X (count x n uint16, host) on `stream`:
+    mean CUDA-event duration of `reps` back-to-back launches after three warm-up
+    launches (the cost matrix stays L2-resident, as in a generation), against
+    the L2 random-gather rate measured by dpso_probe_l2_gather_gbs on a buffer
+    of the cost matrix's size (at least 8 MiB)."""
+    import numpy as np
+    import torch
+    count = X.shape[0]
+    T = torch.from_numpy(np.ascontiguousarray(X).view(np.int16)).cuda()
+    out = torch.empty(count, dtype=torch.int64, device="cuda")
+    for _ in range(3):
+        dpso.dpso_fitness(C, n, T, count, out, stream)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(reps):
+        dpso.dpso_fitness(C, n, T, count, out, stream)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1) / reps
+    probe_bytes = max(8 << 20, 4 * n * n)
+    peak = dpso.dpso_probe_l2_gather_gbs(probe_bytes, 64, stream)
+    algo = 4 * n * count
+    achieved = algo / (ms / 1e3) / 1e9
+    return {"kernel": "fitness_kernel", "bound": "l2_gather", "bytes_per_launch": algo,
+            "tours": count, "ms_per_launch": ms, "achieved": achieved, "peak": peak,
+            "unit": "GB/s", "frac": achieved / peak if peak else None,
+            "traffic": dram_traffic("fitness_kernel", workload_name),
+            "peak_source": f"random 4-byte gathers from an L2-resident {probe_bytes >> 20} MiB "
+                           "buffer measured in this run by dpso_probe_l2_gather_gbs "
+                           "(best of 5)"}
+
+
 def dram_traffic(kernel: str, workload_name: str):
     """DRAM bytes per launch of `kernel` on `workload_name` from the committed
     ncu summary, if it was taken from the current kernel source (else None)."""

@@ -129,3 +129,23 @@ def test_clock_samples_are_kept_only_inside_the_timed_window(tmp_path):
     got = cs.summary()
     assert got["samples"] == 2 and got["samples_all"] == 4
     assert got["sm_mhz"] == 2055.0 and got["reasons"] == []
+
+
+def test_every_global_name_the_bench_uses_exists():
+    # the GPU legs only run on a GPU machine: a name they use that the module does
+    # not define must still fail here
+    import builtins
+    import dis
+    import types
+
+    def globals_of(code):
+        for ins in dis.get_instructions(code):
+            if ins.opname == "LOAD_GLOBAL":
+                yield ins.argval
+        for const in code.co_consts:
+            if isinstance(const, types.CodeType):
+                yield from globals_of(const)
+    missing = sorted({name for name in globals_of(compile(open(bench.__file__).read(),
+                                                          bench.__file__, "exec"))
+                      if not hasattr(bench, name) and not hasattr(builtins, name)})
+    assert not missing, missing

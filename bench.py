@@ -68,7 +68,7 @@ def workload(name: str):
         return inputs.batched()[0]
     if name == "serving":      # ... or the first request of the stream
         return inputs.serving(count=1)[0][1]
-    if name == "astar":        # ... or the facade's swarm
+    if name in ("astar", "two-opt"):  # ... or the facade's swarm
         return inputs.facade()
     return inputs.CONFIGS[name]()
 
@@ -731,6 +731,51 @@ def astar_line(args):
     }
 
 
+def two_opt_line(args):
+    """Standalone edge exchange: dpso_two_opt over `--tours` random tours of the
+    facade or bridge instance, each taken through at most `--max-moves` moves
+    (0: to 2-optimality), timed with CUDA events per call.  A small, bounded
+    case of the swarm's 2-opt kernel shapes (the launch shape follows the tour
+    count), e.g. for ncu captures."""
+    import numpy as np
+    import torch
+
+    from paper_1706_04399_gb300 import dpso, inputs
+
+    inst = inputs.CONFIGS[args.two_opt_instance]()
+    n = inst.n
+    stream = torch.cuda.current_stream()
+    C = torch.empty((n, n), dtype=torch.int32, device="cuda")
+    dpso.dpso_cost_matrix(torch.from_numpy(inst.xyz).cuda(), n, torch.from_numpy(inst.boxes).cuda(),
+                          inst.m, dpso.default_cost_params(), C, stream)
+    tours = inputs.random_tours(n, args.tours, 5)
+    cost = torch.empty(args.tours, dtype=torch.int64, device="cuda")
+    ms, pairs, moves = [], 0, 0
+    for k in range(args.warmup + args.steps):
+        T = torch.from_numpy(tours.view(np.int16).copy()).cuda()
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        pairs, moves = dpso.dpso_two_opt(C, n, T, args.tours, cost, args.max_moves, stream)
+        e1.record(stream)
+        torch.cuda.synchronize()
+        if k >= args.warmup:
+            ms.append(e0.elapsed_time(e1))
+    mean = sum(ms) / len(ms)
+    return {
+        "metric": METRIC, "value": pairs / (mean / 1e3), "unit": "2-opt candidate pairs/s",
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "ms_per_step": mean,
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "i32",
+        "data": "synthetic",
+        "config": {"workload": f"two-opt-{inst.name}-{n}vp-{args.tours}tours",
+                   "n": n, "tours": args.tours, "max_moves": args.max_moves,
+                   "what": "dpso_two_opt on the same random tours each step (plain-scan pairs)",
+                   "l2": "cost matrix L2-resident after the first call"},
+        "two_opt_pairs": pairs, "two_opt_moves_applied": moves,
+        "gpu_launches": None, "roofline": None, "cpu_baseline": None, "e2e": None,
+    }
+
+
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -738,9 +783,14 @@ def main(argv=None):
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--workload", default="facade",
-                    choices=["tiny", "facade", "bridge", "batched", "serving", "astar"])
+                    choices=["tiny", "facade", "bridge", "batched", "serving", "astar",
+                             "two-opt"])
     ap.add_argument("--astar-instance", default="facade", choices=["facade", "bridge"],
                     help="astar: whose viewpoints and boxes")
+    ap.add_argument("--two-opt-instance", default="bridge", choices=["facade", "bridge"],
+                    help="two-opt: whose cost matrix")
+    ap.add_argument("--tours", type=int, default=152, help="two-opt: random tours per call")
+    ap.add_argument("--max-moves", type=int, default=30, help="two-opt: move cap per tour")
     ap.add_argument("--instances", type=int, default=256, help="batched: instances")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests")
     ap.add_argument("--max-n", type=int, default=400, help="serving: largest request taken")
@@ -762,6 +812,8 @@ def main(argv=None):
         out = serving_line(args)
     elif args.workload == "astar":
         out = astar_line(args)
+    elif args.workload == "two-opt":
+        out = two_opt_line(args)
     else:
         out = gpu_line(args)
     if out is not None:

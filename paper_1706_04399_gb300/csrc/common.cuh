@@ -228,6 +228,8 @@ __host__ __device__ inline int shifted_ld(int n) {
 }
 size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages);
 int two_opt_tiled_rows(int n);  // default tile height, 0 when no height fits
+// Shape of a launch over `count` tours with no pinned shape (rows 0: none fits).
+void two_opt_default_shape(int n, int count, int num_sms, int* rows, int* tpc, int* tg);
 int two_opt_tiled_tpc(int n, int rows);  // default tours per CTA
 int two_opt_tiled_tg(int n, int rows, int tpc);  // default tiles in flight per tour
 int two_opt_tiled_ctas(int n, int rows, int tpc, int tg);  // resident CTAs per SM

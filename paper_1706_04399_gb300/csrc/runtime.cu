@@ -1214,9 +1214,15 @@ int dpso_batch_autotune(dpso_batch* b, dpso_two_opt_shape* chosen, void* stream)
         *chosen = dpso_two_opt_shape{0, 0, 0};
         if (!b->cls.empty()) {
             const TwoOptBatch& tb = b->cls[0].tb;
-            const int rows = tb.rows > 0 ? tb.rows : two_opt_tiled_rows(tb.max_n);
-            const int tpc = tb.tpc > 0 ? tb.tpc : (rows > 0 ? two_opt_tiled_tpc(tb.max_n, rows) : 0);
-            const int tg = tb.tg > 0 ? tb.tg : (rows > 0 ? two_opt_tiled_tg(tb.max_n, rows, tpc) : 0);
+            int rows = tb.rows, tpc = tb.tpc, tg = tb.tg;
+            if (rows <= 0) {  // the class runs the default shape for its tours
+                int sms = 0;
+                CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, b->device));
+                two_opt_default_shape(tb.max_n, tb.total, sms, &rows, &tpc, &tg);
+            } else {
+                if (tpc <= 0) tpc = two_opt_tiled_tpc(tb.max_n, rows);
+                if (tg <= 0) tg = two_opt_tiled_tg(tb.max_n, rows, tpc);
+            }
             *chosen = dpso_two_opt_shape{rows, tpc, tg};
         }
     }

@@ -245,9 +245,13 @@ cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     if (b.total <= 0) return cudaSuccess;
     if (b.kind == 1) return launch_node_swap_tiled(b, num_sms, st);
     if (b.shifted && two_opt_tiled_rows(b.max_n) > 0) {
-        const int rows = b.rows > 0 ? b.rows : two_opt_tiled_rows(b.max_n);
-        const int tpc = b.tpc > 0 ? b.tpc : two_opt_tiled_tpc(b.max_n, rows);
-        const int tg = b.tg > 0 ? b.tg : two_opt_tiled_tg(b.max_n, rows, tpc);
+        int rows = b.rows, tpc = b.tpc, tg = b.tg;
+        if (rows <= 0) {  // no pinned shape
+            two_opt_default_shape(b.max_n, b.total, num_sms, &rows, &tpc, &tg);
+        } else {
+            if (tpc <= 0) tpc = two_opt_tiled_tpc(b.max_n, rows);
+            if (tg <= 0) tg = two_opt_tiled_tg(b.max_n, rows, tpc);
+        }
         return launch_two_opt_tiled(b, rows, tpc, tg, num_sms, st);
     }
     return launch_two_opt_general(b, num_sms, st);

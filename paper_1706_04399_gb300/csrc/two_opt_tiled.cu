@@ -127,6 +127,10 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
     static_assert(TG == 1 || TPC == 1, "two tile subgroups need the whole CTA");
     constexpr int kRows = ROWS;        // positions per tile, one per lane
     constexpr int kStaged = ROWS + 1;  // cost rows staged per tile
+    // Tiles of 16 or 8 rows (long tours) split each warp into 2 or 4 lane
+    // groups that evaluate the same rows over different column ranges, so no
+    // lane idles; the groups' minima per row meet by shuffles.
+    constexpr int SPLIT = ROWS == 8 ? 4 : (ROWS == 16 ? 2 : 1);
     constexpr int WPT = kWarps * TG / TPC;  // warps per tour
     constexpr int WSG = WPT / TG;           // warps per tile subgroup
     constexpr int GT = WPT * 32;            // threads per tour
@@ -325,9 +329,14 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                 }
                 stage_wait();
                 const bool full = s_mode[sg] != 0;
-                // lanes past the tile height idle on a valid row; byte offsets
-                // of this lane's two rows (row start plus its 0..3 word shift)
-                const int ra = min(lane, kRows - 1), rb1 = min(lane + 1, kRows);
+                // the row this lane evaluates (lanes past the tile height idle
+                // on a valid row unless the tile splits the warp); byte offsets
+                // of its two staged rows (row start plus its 0..3 word shift)
+                const int lrow = SPLIT > 1 ? (lane & (kRows - 1)) : min(lane, kRows - 1);
+                const int part = SPLIT > 1 ? lane / kRows : 0;
+                const int ie = I + lrow;
+                const bool eval_ok = (SPLIT > 1 || lane < kRows) && ie <= n - 3;
+                const int ra = lrow, rb1 = lrow + 1;
                 const int p1 = half * buf_words + ra * ldq + ((ra >> 3) & 3);
                 const int p2 = half * buf_words + rb1 * ldq + ((rb1 >> 3) & 3);
                 const char* const r1 = reinterpret_cast<const char*>(smi + p1);
@@ -352,12 +361,18 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                     const unsigned tc = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(cnt));
                     if (lane == 0) s_evals[sg] += tc;
                 }
+                // this lane group's share of the warp's groups
+                int h0 = g0, h1 = g1;
+                if constexpr (SPLIT > 1) {
+                    h0 = g0 + ((g1 - g0) * part) / SPLIT;
+                    h1 = g0 + ((g1 - g0) * (part + 1)) / SPLIT;
+                }
                 // first valid column of this lane's row (rows past n-3 have none)
-                const int lim = row_ok ? i + 2 : INT_MAX;
+                const int lim = eval_ok ? ie + 2 : INT_MAX;
                 int m = INT_MAX, cm = 0;
-                int c = cstart + 4 * g0;
-                const int cend = cstart + 4 * g1;
-                int q = g0 < g1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
+                int c = cstart + 4 * h0;
+                const int cend = cstart + 4 * h1;
+                int q = h0 < h1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
                 const int4* rp = smi4 + ((rec2 + c) >> 1);   // records c .. c+3
                 auto at = [](const char* row, int off) {
                     return *reinterpret_cast<const int*>(row + off);
@@ -385,8 +400,14 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                 const int cmask = min(cend, I + kStaged);
                 while (c < cmask) group(true);
                 while (c < cend) group(false);
-                if (m != INT_MAX && row_ok)
-                    atomicMin(&rowkey[i], pack_key(m + smi2[rec2 + i].y, i, cm));
+                unsigned long long key = m != INT_MAX && eval_ok
+                                             ? pack_key(m + smi2[rec2 + ie].y, ie, cm)
+                                             : ~0ull;
+                if constexpr (SPLIT > 1) {  // the lane groups sharing a row
+                    key = min(key, __shfl_xor_sync(0xffffffffu, key, 16));
+                    if constexpr (SPLIT == 4) key = min(key, __shfl_xor_sync(0xffffffffu, key, 8));
+                }
+                if (part == 0 && key != ~0ull) atomicMin(&rowkey[ie], key);
                 if (TG == 2 && wsg == 0 && lane == 0)
                     s_tile[sg * 2 + (par ^ 1)] =
                         tlast - static_cast<int>(atomicAdd(&s_next[grp], 1u));
@@ -570,6 +591,24 @@ int two_opt_tiled_rows(int n) {
 
 int two_opt_tiled_tpc(int n, int rows) {
     return n <= 256 && two_opt_tiled_fits(n, rows, 2, 1) ? 2 : 1;
+}
+
+// The launch shape used when none is pinned.  Long tours whose tallest
+// fitting tile has 16 rows or fewer take 8-row tiles with two tours per CTA
+// when those fit and the launch has at least two tours per SM: with the warps
+// split over column ranges, two tours in flight per SM beat one (2.17 s
+// against 2.49 s per steady-state generation of 4096 tours at n = 1992); with
+// fewer tours, pairing them would leave SMs idle.
+void two_opt_default_shape(int n, int count, int num_sms, int* rows, int* tpc, int* tg) {
+    *rows = two_opt_tiled_rows(n);
+    *tpc = *rows > 0 ? two_opt_tiled_tpc(n, *rows) : 0;
+    *tg = *rows > 0 ? two_opt_tiled_tg(n, *rows, *tpc) : 0;
+    if (*rows > 0 && *rows <= 16 && n > 256 && count >= 2 * num_sms &&
+        two_opt_tiled_fits(n, 8, 2, 1)) {
+        *rows = 8;
+        *tpc = 2;
+        *tg = 1;
+    }
 }
 
 cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStream_t st) {

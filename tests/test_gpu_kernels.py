@@ -177,6 +177,15 @@ def test_two_opt_large_tiles_capped_bitwise(n, moves):
     _two_opt_case(C_np, inputs.random_tours(n, 3, n), max_moves=moves)
 
 
+def test_two_opt_long_tours_two_per_cta_bitwise():
+    # 1906 <= n <= 2081 with at least two tours per SM takes 8-row tiles, two
+    # tours per CTA and four lane groups per warp by default; capped moves keep
+    # the oracle to a few passes per tour
+    n, count = 1992, 320
+    C_np = inputs.random_cost_matrix(n, 19, hi=1_000_000)
+    _two_opt_case(C_np, inputs.random_tours(n, count, 20), max_moves=2)
+
+
 @pytest.mark.parametrize("n", [37, 101, 403])
 def test_two_opt_extreme_costs_bitwise(n):
     # entries at the top of the allowed range: the padding columns past n must

@@ -352,6 +352,16 @@ int dpso_batch_autotune(dpso_batch *b, dpso_two_opt_shape *chosen, void *stream)
  * copies the tiled kernel reads.  Results do not depend on the shape.
  * Synchronises the batch's stream. */
 int dpso_batch_set_two_opt_shape(dpso_batch *b, const dpso_two_opt_shape *shape);
+/* The 2-opt launch shape used when none is pinned, for a launch over `count`
+ * tours of n viewpoints on a GPU with `num_sms` SMs (a launch implementation
+ * choice; the paper has none).  Up to n = 256: 32-row tiles, two tours per
+ * CTA; beyond: the shape with the most tile rows in flight per SM, except that
+ * tours whose tallest fitting tile has 16 rows or fewer take 8-row tiles with
+ * two tours per CTA when those fit and count >= 2 * num_sms.  All zero when
+ * no tiled shape fits (the general kernel runs).  Host only, no device call.
+ * DPSO_ERR_ARG for a NULL out, n < 3, count < 0 or num_sms < 1. */
+int dpso_two_opt_default_shape(int32_t n, int32_t count, int32_t num_sms,
+                               dpso_two_opt_shape *out);
 void dpso_batch_destroy(dpso_batch *b);
 
 /*

@@ -1229,6 +1229,17 @@ int dpso_batch_autotune(dpso_batch* b, dpso_two_opt_shape* chosen, void* stream)
     return DPSO_OK;
 }
 
+int dpso_two_opt_default_shape(int32_t n, int32_t count, int32_t num_sms,
+                               dpso_two_opt_shape* out) {
+    if (!out || n < 3 || count < 0 || num_sms < 1) return DPSO_ERR_ARG;
+    *out = dpso_two_opt_shape{0, 0, 0};
+    if (n > DPSO_MAX_N) return DPSO_OK;
+    int rows = 0, tpc = 0, tg = 0;
+    two_opt_default_shape(n, count, num_sms, &rows, &tpc, &tg);
+    if (rows > 0) *out = dpso_two_opt_shape{rows, tpc, tg};
+    return DPSO_OK;
+}
+
 int dpso_batch_set_two_opt_shape(dpso_batch* b, const dpso_two_opt_shape* shape) {
     if (!b) return DPSO_ERR_ARG;
     DeviceGuard g(b->device);

@@ -133,6 +133,8 @@ def lib():
             "dpso_cost_matrix": (ctypes.c_int, [_vp, _i32, _vp, _i32,
                                                 ctypes.POINTER(dpso_cost_params), _vp, _vp]),
             "dpso_fitness": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _vp]),
+            "dpso_two_opt_default_shape": (ctypes.c_int, [_i32, _i32, _i32,
+                                                          ctypes.POINTER(dpso_two_opt_shape)]),
             "dpso_probe_l2_gather_gbs": (ctypes.c_int, [ctypes.c_size_t, _i32,
                                                         ctypes.POINTER(ctypes.c_double), _vp]),
             "dpso_two_opt": (ctypes.c_int, [_vp, _i32, _vp, _i32, _vp, _i32, _i64p, _i64p, _vp]),
@@ -299,6 +301,15 @@ def dpso_probe_l2_read_gbs(nbytes: int = 24 << 20, reps: int = 40, stream=None) 
     _check(lib().dpso_probe_l2_read_gbs(nbytes, reps, ctypes.byref(out), _stream(stream)),
            "dpso_probe_l2_read_gbs")
     return out.value
+
+
+def dpso_two_opt_default_shape(n: int, count: int, num_sms: int) -> tuple[int, int, int]:
+    """(tile rows, tours per CTA, tiles in flight) a launch over `count` tours
+    of n viewpoints takes when no shape is pinned; (0, 0, 0): the general kernel."""
+    sh = dpso_two_opt_shape()
+    _check(lib().dpso_two_opt_default_shape(n, count, num_sms, ctypes.byref(sh)),
+           "dpso_two_opt_default_shape")
+    return sh.rows, sh.tours_per_cta, sh.tiles_in_flight
 
 
 def dpso_probe_l2_gather_gbs(nbytes: int = 16 << 20, reps: int = 64, stream=None) -> float:

@@ -134,3 +134,23 @@ def test_binding_structs_match_the_header(tmp_path):
         assert int(got[s.__name__]) == ctypes.sizeof(s), s.__name__
         for f, _ in s._fields_:
             assert int(got[f"{s.__name__}.{f}"]) == getattr(s, f).offset, (s.__name__, f)
+
+
+def test_default_two_opt_shapes(libpath):
+    # host-only: the launch shapes used when none is pinned (results never
+    # depend on the shape; these pin the documented choice)
+    from paper_1706_04399_gb300 import dpso
+    shape = dpso.dpso_two_opt_default_shape
+    assert shape(200, 1024, 152) == (32, 2, 1)       # short tours: two per CTA
+    assert shape(400, 1024, 152) == (32, 1, 2)       # the facade: two tiles in flight
+    assert shape(1992, 4096, 152) == (8, 2, 1)       # the bridge: 8-row tiles, two tours
+    assert shape(1992, 152, 152) == (16, 1, 1)       # too few tours to pair them
+    assert shape(1992, 303, 152) == (16, 1, 1)
+    assert shape(1992, 304, 152) == (8, 2, 1)
+    assert shape(2600, 4096, 152)[0] == 16           # two 8-row tours no longer fit
+    assert shape(6600, 10, 152) == (0, 0, 0)         # beyond the tiled kernel
+    L = dpso.lib()
+    out = dpso.dpso_two_opt_shape()
+    assert L.dpso_two_opt_default_shape(2, 1, 152, ctypes.byref(out)) == dpso.ERR_ARG
+    assert L.dpso_two_opt_default_shape(400, 1, 0, ctypes.byref(out)) == dpso.ERR_ARG
+    assert L.dpso_two_opt_default_shape(400, 1, 152, None) == dpso.ERR_ARG

@@ -132,8 +132,8 @@ def test_clock_samples_are_kept_only_inside_the_timed_window(tmp_path):
 
 
 def test_every_global_name_the_bench_uses_exists():
-    # the GPU legs only run on a GPU machine: a name they use that the module does
-    # not define must still fail here
+    # the GPU legs only run where a GPU is present: a name they use that the
+    # module does not define must still fail here
     import builtins
     import dis
     import types

@@ -763,3 +763,19 @@ def test_astar_squared_heuristic_trap(oracle_mod):
     pts = np.array([[3.5, 3.5, 0.5], [0.5, 2.5, 0.5]])
     C, st = oracle_mod.cost_matrix_astar(pts, occ, (0, 0, 0), 1.0, (5, 4, 1), unit_mm=1)
     assert st == 0 and C[0, 1] == 6
+
+
+def test_fitness_sums_past_the_int32_range(oracle_mod):
+    # Eq. (min) over a complete graph whose off-diagonal costs are all K: any
+    # tour costs exactly n*K, here far past 2^31 (the sum must be 64-bit)
+    n, K = 400, 1 << 29
+    C = np.full((n, n), K, dtype=np.int32)
+    np.fill_diagonal(C, 0)
+    rng = np.random.default_rng(3)
+    for _ in range(3):
+        x = rng.permutation(n).astype(np.uint16)
+        assert oracle_mod.fitness(C, x) == n * K
+    # one cheaper edge pair on the tour lowers the cost by exactly its saving
+    x = np.arange(n, dtype=np.uint16)
+    C[5, 6] = C[6, 5] = 7
+    assert oracle_mod.fitness(C, x) == (n - 1) * K + 7

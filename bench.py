@@ -1,22 +1,30 @@
 #!/usr/bin/env python
 """Throughput benchmark of the GB300 DPSO hot path.
 
-Workload: the office-facade-shaped instance (400 viewpoints on a 20x20 grid
-over a 40 m x 30 m wall, 3 m stand-off, +-0.2 m jitter, 5 random boxes),
-swarm 1024, the paper's w = 1, phi1 = phi2 = 0.4, mutation every third
-generation, back-and-forth seeding and edge exchange on.  A step is one DPSO
-generation (Fig. "pseudocode"): particle update + fitness + pbest, mutation
-when due, gbest, and the edge exchange whenever the gbest did not improve.
+Workload (default): the bridge-shaped instance (1992 viewpoints over seven
+planar faces of a deck and two piers at 1 m spacing and 2 m stand-off, 20
+boxes), swarm 4096, the paper's w = 1, phi1 = phi2 = 0.4, mutation every
+third generation, back-and-forth seeding and edge exchange on.  `--workload
+facade` takes the office-facade-shaped instance (400 viewpoints, swarm 1024).
+A step is one DPSO generation (Fig. "pseudocode"): particle update + fitness +
+pbest, mutation when due, gbest, and the edge exchange whenever the gbest did
+not improve.
 
-value   particle-iterations/s = particles x generations / device time, with the
-        cost matrix and swarm resident in HBM; the L2 is flushed between timed
+value   particle-iterations/s = particles x generations / device time of the
+        generations dpso_step replays from its CUDA graphs, with the cost
+        matrix and swarm resident in HBM; the L2 is flushed between timed
         generations.  For N > 1 each rank runs an independent replica (the
         solver has no exchange step to shard).
+2-opt moves/s  candidate 2-opt pairs the exchange kernel evaluated per second
+        of its own device time (`two_opt_pairs_evaluated_per_s`); the pairs a
+        plain best-improvement scan of the same passes would take are
+        reported beside it.
 e2e     the same metric through dpso_plan from pinned host buffers: copies in,
         cost matrix, initialisation, `steps` generations, best tour out.
-roofline  the 2-opt kernel: 8 bytes of C per candidate pair (two int32 entries)
-        over its CUDA-event time, against the L2 read bandwidth measured in
-        this run (the cost matrix is L2-resident; rows are staged from L2).
+roofline  the 2-opt kernel: 8 bytes of C per candidate pair evaluated (two
+        int32 entries) over its CUDA-event time inside the timed generations,
+        against the L2 read bandwidth measured in this run (the cost matrix is
+        L2-resident; rows are staged from L2).
 fitness_roofline  the tour-fitness kernel (Eq. min) over the swarm's tours:
         4 n bytes of C gathered per tour over its CUDA-event time, against the
         random 4-byte gather rate from an L2-resident buffer measured in this
@@ -42,17 +50,29 @@ METRIC = "DPSO particle-iterations/s and 2-opt moves/s per GB300; batched p99 la
 UNIT = "particle-iterations/s"
 BYTES_PER_PAIR = 8          # 2-opt: C[x_i][x_j] + C[x_i+1][x_j+1], int32 each
 BYTES_PER_SWAP_PAIR = 16    # node swap: the four new edges' costs, int32 each
-CPU_SAMPLE_SWARM = 16       # oracle sample: particles
-CPU_SAMPLE_GENERATIONS = 10 # oracle sample: generations
+DEFAULT_STEPS = {"bridge": 20, "facade": 100, "tiny": 100, "batched": 3, "astar": 20,
+                 "two-opt": 3, "serving": 1}
 
 
-def cpu_sample_shape(n: int, node_swap: bool = False) -> tuple[int, int]:
-    """(particles, generations) of the oracle sample, sized to a few tens of
-    seconds on one core: the oracle's first generations cost about n^3 per
-    particle (2-opt from the initial tours), the node swap about twice that."""
+def cpu_sample_shape(n: int, threads: int, node_swap: bool = False) -> tuple[int, int]:
+    """(particles, generations) of the oracle sample for the bench's
+    cpu_baseline, sized to a few tens of seconds on `threads` host threads
+    (each particle's edge exchange runs on one thread): an early generation
+    costs the oracle about n^3 per particle (2-opt from the initial tours),
+    about 0.1 s at n = 400 and 10-30 s at n = 1992; the node swap about twice
+    the 2-opt."""
+    if n > 1000:
+        return threads, 1
     if n > 600:
-        return 4, 1
-    return CPU_SAMPLE_SWARM, (4 if node_swap else CPU_SAMPLE_GENERATIONS)
+        return 2 * threads, 1
+    return 8 * threads, (2 if node_swap else 4)
+
+
+def reference_swarm(n: int, threads: int) -> int:
+    """Particles of the reference arm's oracle swarm: one per host thread for
+    the long tours (a generation then costs about one particle's exchange,
+    5-30 s at n = 1992), more for short ones."""
+    return threads if n > 1000 else (4 * threads if n > 300 else 8 * threads)
 
 
 def _env_int(name, default):
@@ -93,19 +113,33 @@ def cpu_model() -> str:
 
 # ----------------------------------------------------------------- CPU oracle
 
-def oracle_sample(inst, swarm: int, warmup: int, generations: int, flags=None):
-    """Times the oracle (single thread) on `generations` generations of a
-    `swarm`-particle swarm over the same instance; returns (value, seconds)."""
+def oracle_sample(inst, swarm: int, warmup: int, generations: int, threads: int, flags=None):
+    """Times the oracle on `generations` generations of a `swarm`-particle
+    swarm over the same instance, the edge exchange of each particle on one
+    of `threads` host threads (the oracle's arithmetic is its plain
+    single-threaded C; particles' exchanges are independent); returns
+    (value, seconds)."""
     import oracle
     C, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
     sw = oracle.Swarm(C, inst.tags, swarm=swarm, seed=inst.seed,
                       flags=oracle.ALL if flags is None else flags)
-    if warmup:
-        sw.run(warmup)
+    for _ in range(warmup):
+        sw.iterate_threaded(threads)
     t0 = time.perf_counter()
-    sw.run(generations)
+    for _ in range(generations):
+        sw.iterate_threaded(threads)
     dt = time.perf_counter() - t0
     return swarm * generations / dt, dt
+
+
+def swarm_config(inst, exchange: str, world: int, steps: int) -> dict:
+    """The `config` of a swarm workload's bench line (both arms)."""
+    node_swap = exchange == "node-swap"
+    return {"workload": f"{inst.name}-{inst.n}vp-{inst.swarm}p" + ("-nodeswap" if node_swap else ""),
+            "n": inst.n, "swarm": inst.swarm, "exchange": exchange,
+            "generations_timed": steps, "boxes": inst.m,
+            "l2": "flushed between timed generations (256 MiB write)",
+            "parallelism": "replicas" if world > 1 else "single"}
 
 
 def run_reference(args):
@@ -113,27 +147,35 @@ def run_reference(args):
     if rank != 0:
         return 0
     inst = workload(args.workload)
-    per_step = []
     import oracle
+    node_swap = args.exchange == "node-swap"
+    flags = oracle.ALL | (oracle.NODE_SWAP if node_swap else 0)
     C, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
-    swarm, _ = cpu_sample_shape(inst.n)
-    sw = oracle.Swarm(C, inst.tags, swarm=swarm, seed=inst.seed)
-    sw.run(args.warmup)
+    threads = cpu_cores()
+    swarm = reference_swarm(inst.n, threads)
+    sw = oracle.Swarm(C, inst.tags, swarm=swarm, seed=inst.seed, flags=flags)
+    for _ in range(args.warmup):
+        sw.iterate_threaded(threads)
+    per_step = []
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        sw.iterate()
+        sw.iterate_threaded(threads)
         per_step.append(time.perf_counter() - t0)
     total = sum(per_step)
     value = swarm * args.steps / total
-    sample = (f"{inst.name} instance (n={inst.n}), oracle swarm of {swarm} particles "
-              f"instead of {inst.swarm}, {args.warmup} untimed + {args.steps} timed generations")
+    sample = (f"{inst.name} instance (n={inst.n}): an oracle swarm of {swarm} particles "
+              f"(the workload's is {inst.swarm}) from its own initial swarm, "
+              f"{args.warmup} untimed + {args.steps} timed generations, each particle's edge "
+              f"exchange on one of {threads} host threads")
+    config = swarm_config(inst, args.exchange, args.gpus, args.steps)
+    config["sample_swarm"] = swarm
     line = {
         "impl": "reference", "metric": METRIC, "value": value, "unit": UNIT,
         "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1000 * total / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-        "config": {"workload": f"{inst.name}-{inst.n}vp", "n": inst.n, "swarm": inst.swarm},
-        "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
+        "config": config,
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": threads, "kind": "oracle",
                          "sample": sample, "cpu": cpu_model()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
@@ -349,10 +391,12 @@ def gpu_line(args):
     sw = dpso.Swarm(C, n, inst.tags, params, seed, stream)
     sampler = ClockSampler(gpu_index_for_smi(local))
     sampler.__enter__()            # sampling from here; the timed window is marked below
-    sw.set_timing(True)
     sw.step(args.warmup, stream)
     torch.cuda.synchronize()
-    sw.set_timing(True)            # clears the accumulators: only timed steps count
+    # timing mode: the same generation graphs, their phase-boundary event
+    # nodes pointed at fresh events before every replay (turning it on clears
+    # the accumulators, so only the timed generations count)
+    sw.set_timing(True)
     st0 = sw.stats()
 
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
@@ -412,12 +456,16 @@ def gpu_line(args):
         fit_roof = fitness_roofline(dpso, C, n, sw.state()["X"], stream, inst.name)
         cpu = None
         if world == 1 and not args.no_cpu_baseline:
-            cs, cg = cpu_sample_shape(n, node_swap)
-            cval, csec = oracle_sample(inst, cs, 0, cg, flags)
-            cpu = {"value": cval, "unit": UNIT, "cores": 1, "kind": "oracle",
-                   "sample": f"{inst.name} instance (n={n}), oracle swarm of {cs} "
-                             f"particles, first {cg} generations "
-                             f"({csec:.1f} s)",
+            threads = cpu_cores()
+            cs, cg = cpu_sample_shape(n, threads, node_swap)
+            cval, csec = oracle_sample(inst, cs, 0, cg, threads, flags)
+            cpu = {"value": cval, "unit": UNIT, "cores": threads, "kind": "oracle",
+                   "sample": f"{inst.name} instance (n={n}), an oracle swarm of {cs} "
+                             f"particles from its own initial swarm, generations 1..{cg} "
+                             f"({csec:.1f} s; early generations exchange from random "
+                             f"tours and cost the oracle more per particle than the timed "
+                             f"steady state), each particle's edge exchange on one of "
+                             f"{threads} host threads",
                    "host_cores": cpu_cores(), "cpu": cpu_model()}
         e2e = None
         if not args.no_e2e:
@@ -442,19 +490,22 @@ def gpu_line(args):
                    "what": f"dpso_plan: {args.steps} generations from host buffers, including "
                            "cost matrix and initialisation"}
         phases = {k: round(v, 3) for k, v in timing["ms"].items()}
+        config = swarm_config(inst, args.exchange, world, args.steps)
+        config["timed_path"] = ("dpso_step replaying its generation graphs (timing mode: the "
+                                "graphs' phase-boundary event nodes bound to fresh events)")
         out = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": dev_ms_max / args.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "i32", "data": "synthetic",
-            "config": {"workload": f"{inst.name}-{n}vp-{S}p" + ("-nodeswap" if node_swap else ""),
-                       "n": n, "swarm": S, "exchange": args.exchange,
-                       "generations_timed": args.steps, "boxes": inst.m,
-                       "l2": "flushed between timed generations (256 MiB write)",
-                       "parallelism": "replicas" if world > 1 else "single"},
-            "two_opt_pairs_per_s": pairs / (two_ms / 1e3) if two_ms > 0 else 0.0,
-            "two_opt_moves_applied": moves, "two_opt_pairs": pairs,
+            "config": config,
+            # the metric's "2-opt moves/s": candidate pairs the kernel evaluated
+            "two_opt_pairs_evaluated_per_s": evaluated / (two_ms / 1e3) if two_ms > 0 else 0.0,
             "two_opt_pairs_evaluated": evaluated,
+            # what a plain best-improvement scan of the same passes would take
+            "two_opt_plain_scan_pairs": pairs,
+            "two_opt_plain_scan_pairs_per_s": pairs / (two_ms / 1e3) if two_ms > 0 else 0.0,
+            "two_opt_moves_applied": moves,
             "phase_ms": phases, "wall_s": wall,
             "roofline": roofline, "fitness_roofline": fit_roof, "cpu_baseline": cpu, "e2e": e2e,
             "gpu_launches": launches, "clocks": sampler.summary(),
@@ -779,10 +830,11 @@ def two_opt_line(args):
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default by workload: bridge 20, facade 100, ...)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--workload", default="facade",
+    ap.add_argument("--workload", default="bridge",
                     choices=["tiny", "facade", "bridge", "batched", "serving", "astar",
                              "two-opt"])
     ap.add_argument("--astar-instance", default="facade", choices=["facade", "bridge"],
@@ -802,6 +854,8 @@ def main(argv=None):
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)
+    if args.steps is None:
+        args.steps = DEFAULT_STEPS.get(args.workload, 20)
     if args.warmup < 3 and args.impl == "gb300":
         print("note: fewer than 3 warm-up steps", file=sys.stderr)
     if args.impl == "reference":

@@ -288,10 +288,12 @@ int dpso_get_history(dpso_swarm *s, int64_t *gbest_host, int32_t cap, int32_t *l
 int dpso_get_stats(dpso_swarm *s, dpso_stats *st);
 
 /*
- * Timing mode (tracing): while on, dpso_step launches each generation's
- * kernels directly (not from a CUDA graph) with CUDA events between the
- * phases; dpso_get_timing synchronises and returns the accumulated times.
- * Turning it on clears the accumulators.  Results are identical either way.
+ * Timing mode (tracing): each generation graph that dpso_step replays holds
+ * event-record nodes at its phase boundaries; while timing is on, dpso_step
+ * points them at fresh CUDA events before every replay (the same graph, the
+ * same kernels), and dpso_get_timing synchronises and returns the
+ * accumulated phase times.  Turning it on or off clears the accumulators.
+ * Results are identical either way.
  */
 int dpso_set_timing(dpso_swarm *s, int on);
 int dpso_get_timing(dpso_swarm *s, dpso_timing *out);

@@ -103,6 +103,13 @@ def lib():
         L.orc_swarm_gbest.argtypes = [ctypes.c_void_p]
         L.orc_swarm_two_opt.argtypes = [ctypes.c_void_p, _i32p, ctypes.c_int32]
         L.orc_swarm_iterate.argtypes = [ctypes.c_void_p]
+        L.orc_swarm_iterate_begin.argtypes = [ctypes.c_void_p, _i32p]
+        L.orc_swarm_iterate_end.argtypes = [ctypes.c_void_p]
+        L.orc_swarm_two_opt_part.argtypes = [ctypes.c_void_p, _i32p, ctypes.c_int32, _i64p]
+        L.orc_swarm_add_counters.argtypes = [ctypes.c_void_p, ctypes.c_int64, ctypes.c_int64]
+        L.orc_swarm_import.argtypes = [ctypes.c_void_p, _u16p, _u16p, _u16p, _i64p, _i64p, _u16p,
+                                       ctypes.c_int64, ctypes.c_int32, ctypes.c_int32,
+                                       ctypes.c_int32, _i64p, _i64p]
         L.orc_swarm_run.argtypes = [ctypes.c_void_p, ctypes.c_int32]
         for name in ("orc_swarm_n", "orc_swarm_size", "orc_swarm_t", "orc_swarm_done",
                      "orc_swarm_stall", "orc_swarm_last_two_opt", "orc_swarm_last_improved"):
@@ -307,6 +314,73 @@ class Swarm:
     def iterate(self) -> int:
         return lib().orc_swarm_iterate(self._h)
 
+    def iterate_begin(self) -> bool:
+        """The generation up to the edge exchange; True when the exchange runs."""
+        run = np.zeros(1, np.int32)
+        st = lib().orc_swarm_iterate_begin(self._h, _p(run, _i32p))
+        if st < 0:
+            raise RuntimeError(f"oracle generation failed ({st})")
+        return bool(run[0])
+
+    def iterate_end(self):
+        """The rest of the generation after the exchange (gbest, history, stall)."""
+        if lib().orc_swarm_iterate_end(self._h) < 0:
+            raise RuntimeError("iterate_end without iterate_begin")
+
+    def two_opt_part(self, idx):
+        """Exchange of the particles idx only; returns (pairs, moves) without
+        adding them to the swarm's counters.  Calls on disjoint sets of
+        particles may run in concurrent threads (ctypes releases the GIL)."""
+        ii = _c(idx, np.int32)
+        out = np.zeros(2, np.int64)
+        lib().orc_swarm_two_opt_part(self._h, _p(ii, _i32p), ii.shape[0], _p(out, _i64p))
+        return int(out[0]), int(out[1])
+
+    def iterate_threaded(self, threads: int = 1, sample=None):
+        """One generation whose edge exchange runs on `threads` host threads,
+        each on its own particles (the exchange of a particle reads and writes
+        only that particle, so the result is that of iterate()).  With `sample`
+        (particle indices) only those particles are exchanged and the
+        generation is left open: the gbest after the exchange would need every
+        particle.  Returns whether the exchange ran."""
+        from concurrent.futures import ThreadPoolExecutor
+        run = self.iterate_begin()
+        if run:
+            idx = np.arange(self.S, dtype=np.int32) if sample is None else _c(sample, np.int32)
+            # one particle per task, in index order, so long and short
+            # exchanges spread over the threads
+            chunks = [idx[k:k + 1] for k in range(idx.shape[0])]
+            with ThreadPoolExecutor(max(1, threads)) as ex:
+                got = list(ex.map(self.two_opt_part, chunks))
+            lib().orc_swarm_add_counters(self._h, sum(g[0] for g in got), sum(g[1] for g in got))
+        if sample is None or not run:
+            self.iterate_end()
+        return run
+
+    def load_state(self, st: dict):
+        """Snapshot replay: takes the state of another run (same instance and
+        parameters) as a dict with X, P, V (S x n, V as permutations), G, F,
+        PF, gf, t, stall, done, history and optionally pairs, moves, runs."""
+        S, n = self.S, self.n
+        X = _c(st["X"], np.uint16).reshape(S, n)
+        P = _c(st["P"], np.uint16).reshape(S, n)
+        V = _c(st["V"], np.uint16).reshape(S, n)
+        G = _c(st["G"], np.uint16).reshape(n)
+        F = _c(st["F"], np.int64).reshape(S)
+        PF = _c(st["PF"], np.int64).reshape(S)
+        t = int(st["t"])
+        hist = _c(st["history"], np.int64).reshape(-1)
+        if hist.shape[0] != t:
+            raise ValueError("history length differs from t")
+        hist1 = hist if t else np.zeros(1, np.int64)
+        cnt = np.array([st.get("pairs", 0), st.get("moves", 0), st.get("runs", 0)], np.int64)
+        rc = lib().orc_swarm_import(self._h, _p(X, _u16p), _p(P, _u16p), _p(G, _u16p),
+                                    _p(F, _i64p), _p(PF, _i64p), _p(V, _u16p), int(st["gf"]), t,
+                                    int(st.get("stall", 0)), int(bool(st.get("done", False))),
+                                    _p(hist1, _i64p), _p(cnt, _i64p))
+        if rc:
+            raise ValueError(f"oracle rejected the imported state ({rc})")
+
     def run(self, iterations: int) -> int:
         return lib().orc_swarm_run(self._h, iterations)
 
@@ -350,7 +424,10 @@ class Swarm:
         V = np.zeros((S, n), np.uint16)
         lib().orc_swarm_export(self._h, _p(X, _u16p), _p(P, _u16p), _p(G, _u16p),
                                _p(F, _i64p), _p(PF, _i64p), _p(V, _u16p))
-        return {"X": X, "P": P, "G": G, "F": F, "PF": PF, "V": V, "gf": self.gf, "t": self.t}
+        c = self.counters()
+        return {"X": X, "P": P, "G": G, "F": F, "PF": PF, "V": V, "gf": self.gf, "t": self.t,
+                "stall": self.stall, "done": self.done, "history": self.history(),
+                "pairs": c["pairs"], "moves": c["moves"], "runs": c["two_opt_runs"]}
 
     def vel_len(self, p: int) -> int:
         return int(lib().orc_swarm_vel_len(self._h, p))

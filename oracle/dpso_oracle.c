@@ -671,6 +671,10 @@ typedef struct {
     int32_t hist_len, hist_cap;
     int64_t pairs, moves, two_opt_runs;
     int32_t last_improved, last_two_opt;
+    /* a generation between orc_swarm_iterate_begin and _end: its number, the
+     * gbest cost it started from, whether the exchange runs */
+    int32_t gen_t, gen_open, gen_exchange;
+    int64_t gen_gf0;
     uint16_t *scratch; /* 2*(n-1) transpositions */
 } orc_swarm;
 
@@ -984,6 +988,34 @@ void orc_swarm_two_opt(orc_swarm *sw, const int32_t *idx, int32_t count)
     }
 }
 
+/* The edge exchange (then pbest) of particles idx[0..count-1], with its
+ * pair and move counts written to out[0], out[1] instead of being added to
+ * the swarm's counters: it reads and writes only those particles' rows, so
+ * calls on disjoint particle sets may run at the same time.  The caller adds
+ * the counts with orc_swarm_add_counters. */
+void orc_swarm_two_opt_part(orc_swarm *sw, const int32_t *idx, int32_t count, int64_t out[2])
+{
+    int64_t pairs = 0, moves = 0;
+    for (int32_t r = 0; r < count; ++r) {
+        int32_t p = idx[r];
+        if (sw->flags & ORC_NODE_SWAP)
+            moves += orc_node_swap(sw->C, sw->n, row_of(sw->X, sw->n, p), &sw->F[p],
+                                   sw->max_moves, &pairs);
+        else
+            moves += orc_two_opt(sw->C, sw->n, row_of(sw->X, sw->n, p), &sw->F[p],
+                                 sw->max_moves, &pairs);
+        pbest(sw, p);
+    }
+    out[0] = pairs;
+    out[1] = moves;
+}
+
+void orc_swarm_add_counters(orc_swarm *sw, int64_t pairs, int64_t moves)
+{
+    sw->pairs += pairs;
+    sw->moves += moves;
+}
+
 static void hist_put(orc_swarm *sw, int32_t t, int64_t v)
 {
     if (t > sw->hist_cap) {
@@ -1000,13 +1032,24 @@ static void hist_put(orc_swarm *sw, int32_t t, int64_t v)
  * mut_period-th generation, update gbest, and run the edge exchange when the
  * gbest did not strictly improve in this generation (trigger 0), or only in
  * mutation generations that did not improve it (trigger 1, the wording of
- * Sec. 4).  Returns 1 when the loop has stopped (stall limit), else 0. */
-int orc_swarm_iterate(orc_swarm *sw)
+ * Sec. 4).
+ *
+ * The generation is split in two around the exchange so that a caller may
+ * run the exchange itself (it is independent per particle):
+ * orc_swarm_iterate_begin does everything up to the exchange and sets
+ * *run_exchange; orc_swarm_iterate_end does what follows it (gbest, history,
+ * stall).  orc_swarm_iterate runs begin, the exchange of every particle in
+ * index order, and end.  Returns 1 when the loop has stopped (stall limit),
+ * a negative code on error, else 0. */
+int orc_swarm_iterate_begin(orc_swarm *sw, int32_t *run_exchange)
 {
+    *run_exchange = 0;
     if (sw->done)
         return 1;
+    if (sw->gen_open)
+        return ORC_ERR_ARG;
     int32_t t = sw->t + 1;
-    int64_t gf0 = sw->gf;
+    sw->gen_gf0 = sw->gf;
     int st = orc_swarm_move(sw, t);
     if (st)
         return st;
@@ -1014,23 +1057,45 @@ int orc_swarm_iterate(orc_swarm *sw)
     if (mut)
         orc_swarm_mutate(sw, t, NULL);
     orc_swarm_gbest(sw);
-    int improved = sw->gf < gf0;
+    int improved = sw->gf < sw->gen_gf0;
     hist_put(sw, t, sw->gf);
-    int run2 = (sw->flags & ORC_TWO_OPT) && !improved && (sw->trigger == 0 || mut);
-    sw->last_two_opt = run2;
-    if (run2) {
-        orc_swarm_two_opt(sw, NULL, 0);
+    sw->gen_t = t;
+    sw->gen_open = 1;
+    sw->gen_exchange = (sw->flags & ORC_TWO_OPT) && !improved && (sw->trigger == 0 || mut);
+    *run_exchange = sw->gen_exchange;
+    return 0;
+}
+
+int orc_swarm_iterate_end(orc_swarm *sw)
+{
+    if (!sw->gen_open)
+        return ORC_ERR_ARG;
+    int32_t t = sw->gen_t;
+    sw->last_two_opt = sw->gen_exchange;
+    if (sw->gen_exchange) {
         sw->two_opt_runs += 1;
         orc_swarm_gbest(sw);
         hist_put(sw, t, sw->gf);
-        improved = sw->gf < gf0;
     }
+    int improved = sw->gf < sw->gen_gf0;
     sw->last_improved = improved;
     sw->stall = improved ? 0 : sw->stall + 1;
     sw->t = t;
+    sw->gen_open = 0;
     if (sw->stall_limit > 0 && sw->stall >= sw->stall_limit)
         sw->done = 1;
     return 0;
+}
+
+int orc_swarm_iterate(orc_swarm *sw)
+{
+    int32_t run2 = 0;
+    int st = orc_swarm_iterate_begin(sw, &run2);
+    if (st)
+        return st;
+    if (run2)
+        orc_swarm_two_opt(sw, NULL, 0);
+    return orc_swarm_iterate_end(sw);
 }
 
 int orc_swarm_run(orc_swarm *sw, int32_t iterations)
@@ -1086,6 +1151,86 @@ void orc_swarm_export(const orc_swarm *sw, uint16_t *X, uint16_t *P, uint16_t *G
             orc_apply(y, sw->n, sw->V[p].t, sw->V[p].len);
         }
     }
+}
+
+/* Snapshot replay: replaces the swarm's state with one taken from another
+ * run of the same loop (same instance and parameters), so that the next
+ * generations of both can be compared.  Arrays as orc_swarm_export writes
+ * them: X, P (S*n), G (n), F, PF (S), and Vperm (S*n), each velocity given
+ * as the permutation it induces on the identity.  A velocity is stored as the
+ * list Sec. 3.1's subtraction gives for it, (identity + v) - identity: x + v
+ * depends only on that permutation (every transposition swaps two labels),
+ * w.v with w = 1 keeps the list whole, and with w < 1 the list is first
+ * replaced by exactly this canonical list, so the loop continues as it would
+ * from the original lists.  gf, t, stall, done: the loop state; hist: the
+ * t gbest costs so far; counters: the exchange's pairs, moves and runs.
+ * Returns ORC_ERR_ARG, leaving the swarm unchanged, when a row of X, P, G or
+ * Vperm is not a permutation of 0..n-1 or t < 0; ORC_ERR_MEM when out of
+ * memory. */
+static int is_perm(const uint16_t *x, int32_t n, uint8_t *seen)
+{
+    memset(seen, 0, (size_t)n);
+    for (int32_t k = 0; k < n; ++k) {
+        if (x[k] >= n || seen[x[k]])
+            return 0;
+        seen[x[k]] = 1;
+    }
+    return 1;
+}
+
+int orc_swarm_import(orc_swarm *sw, const uint16_t *X, const uint16_t *P, const uint16_t *G,
+                     const int64_t *F, const int64_t *PF, const uint16_t *Vperm, int64_t gf,
+                     int32_t t, int32_t stall, int32_t done, const int64_t *hist,
+                     const int64_t counters[3])
+{
+    int32_t n = sw->n, S = sw->S;
+    if (t < 0 || stall < 0)
+        return ORC_ERR_ARG;
+    uint8_t *seen = (uint8_t *)malloc((size_t)n);
+    uint16_t *id = (uint16_t *)malloc(sizeof(uint16_t) * (size_t)n);
+    if (!seen || !id) {
+        free(seen);
+        free(id);
+        return ORC_ERR_MEM;
+    }
+    int ok = is_perm(G, n, seen);
+    for (int32_t p = 0; p < S && ok; ++p)
+        ok = is_perm(X + (int64_t)p * n, n, seen) && is_perm(P + (int64_t)p * n, n, seen) &&
+             is_perm(Vperm + (int64_t)p * n, n, seen);
+    free(seen);
+    if (!ok) {
+        free(id);
+        return ORC_ERR_ARG;
+    }
+    for (int32_t k = 0; k < n; ++k)
+        id[k] = (uint16_t)k;
+    for (int32_t p = 0; p < S; ++p) {
+        int64_t len = orc_subtract(Vperm + (int64_t)p * n, id, n, sw->scratch);
+        sw->V[p].len = 0;
+        if (vel_append(&sw->V[p], sw->scratch, len)) {
+            free(id);
+            return ORC_ERR_MEM;
+        }
+    }
+    free(id);
+    size_t sn = (size_t)S * (size_t)n;
+    memcpy(sw->X, X, sizeof(uint16_t) * sn);
+    memcpy(sw->P, P, sizeof(uint16_t) * sn);
+    memcpy(sw->G, G, sizeof(uint16_t) * (size_t)n);
+    memcpy(sw->F, F, sizeof(int64_t) * (size_t)S);
+    memcpy(sw->PF, PF, sizeof(int64_t) * (size_t)S);
+    sw->gf = gf;
+    sw->t = t;
+    sw->stall = stall;
+    sw->done = done != 0;
+    sw->gen_open = 0;
+    sw->hist_len = 0;
+    for (int32_t k = 1; k <= t; ++k)
+        hist_put(sw, k, hist[k - 1]);
+    sw->pairs = counters[0];
+    sw->moves = counters[1];
+    sw->two_opt_runs = counters[2];
+    return 0;
 }
 
 int64_t orc_swarm_vel_len(const orc_swarm *sw, int32_t p) { return sw->V[p].len; }

@@ -54,6 +54,11 @@ unsigned long long q32(double c) { return static_cast<unsigned long long>(llroun
 constexpr uint32_t kStateMagic = 0x4f535044u;  // "DPSO"
 constexpr uint32_t kStateVersion = 1;
 
+// Events recorded per generation: before the update, then after the update,
+// the mutation, the first gbest pass, the edge exchange and the second gbest
+// pass.
+constexpr int kPhaseEvents = 6;
+
 struct StateHeader {
     uint32_t magic, version;
     int32_t n, S, t, stall, done, n_det;
@@ -95,10 +100,16 @@ struct dpso_swarm {
     int t_host = 0;
     cudaStream_t last = nullptr;
     cudaStream_t cap = nullptr;
-    cudaGraphExec_t g_plain = nullptr, g_mut = nullptr;
+    // the two generation graphs (index 0: without mutation, 1: with it); each
+    // holds kPhaseEvents event-record nodes at the phase boundaries, which
+    // record into ev_cap unless timing mode rebinds them to pool events
+    cudaGraph_t graph[2] = {nullptr, nullptr};
+    cudaGraphExec_t exec[2] = {nullptr, nullptr};
+    cudaGraphNode_t ev_node[2][kPhaseEvents] = {};
+    cudaEvent_t ev_cap[kPhaseEvents] = {};
     // timing mode
     bool timing = false;
-    std::vector<cudaEvent_t> ev_pool;       // 5 events per timed generation
+    std::vector<cudaEvent_t> ev_pool;       // kPhaseEvents events per timed generation
     std::vector<std::array<int, 2>> pending; // (first event, mutation generation)
     dpso_timing acc{};
 };
@@ -108,8 +119,12 @@ namespace {
 void free_swarm(dpso_swarm* s) {
     if (!s) return;
     for (cudaEvent_t e : s->ev_pool) cudaEventDestroy(e);
-    if (s->g_plain) cudaGraphExecDestroy(s->g_plain);
-    if (s->g_mut) cudaGraphExecDestroy(s->g_mut);
+    for (int k = 0; k < 2; ++k) {
+        if (s->exec[k]) cudaGraphExecDestroy(s->exec[k]);
+        if (s->graph[k]) cudaGraphDestroy(s->graph[k]);
+    }
+    for (cudaEvent_t e : s->ev_cap)
+        if (e) cudaEventDestroy(e);
     void* bufs[] = {s->C,    s->Cs,   s->X,   s->V,     s->P,   s->G,    s->F,    s->PF,
                     s->hash, s->dup,  s->kept, s->order, s->ctl, s->meta, s->hist};
     for (void* b : bufs)
@@ -169,66 +184,60 @@ TwoOptBatch swarm_two_opt(const dpso_swarm* s) {
     return tb;
 }
 
-// Generation kernels for a batch view; `with_mutation` false skips the
-// mutation kernels (they would all be no-ops).  The edge exchange and its
-// gbest pass are gated per instance on the device.
-cudaError_t enqueue_batch_generation(const BatchView& bv, const TwoOptBatch& tb, bool any_two_opt,
-                                     bool with_mutation, int num_sms, cudaStream_t st) {
-    cudaError_t e = launch_move(bv, st);
-    if (e == cudaSuccess && with_mutation) e = launch_mutation(bv, st);
+// One generation of Fig. "pseudocode" for one swarm: particle update,
+// mutation (when due), gbest, then the edge exchange and a second gbest pass
+// (both no-ops unless the first gbest pass scheduled the exchange).  With
+// `ev`, an external event-record node is captured at each phase boundary
+// (move | mutation | gbest | 2-opt | gbest).
+cudaError_t enqueue_generation(dpso_swarm* s, bool mut_iter, cudaStream_t st,
+                               const cudaEvent_t* ev = nullptr) {
+    const bool two = (s->k.flags & DPSO_FLAG_TWO_OPT) != 0;
+    const BatchView bv = swarm_view(s);
+    const TwoOptBatch tb = swarm_two_opt(s);
+    auto mark = [&](int q) {
+        return ev ? cudaEventRecordWithFlags(ev[q], st, cudaEventRecordExternal) : cudaSuccess;
+    };
+    cudaError_t e = mark(0);
+    if (e == cudaSuccess) e = launch_move(bv, st);
+    if (e == cudaSuccess) e = mark(1);
+    if (e == cudaSuccess && mut_iter) e = launch_mutation(bv, st);
+    if (e == cudaSuccess) e = mark(2);
     if (e == cudaSuccess) e = launch_gbest(bv, 0, st);
-    if (e == cudaSuccess && any_two_opt) {
-        e = launch_rank_cost(bv, st);
-        if (e == cudaSuccess) e = cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st);
-        if (e == cudaSuccess) e = launch_two_opt(tb, num_sms, st);
-        if (e == cudaSuccess) e = launch_gbest(bv, 1, st);
-    }
+    if (e == cudaSuccess) e = mark(3);
+    if (e == cudaSuccess && two) e = launch_rank_cost(bv, st);
+    if (e == cudaSuccess && two) e = cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st);
+    if (e == cudaSuccess && two) e = launch_two_opt(tb, s->num_sms, st);
+    if (e == cudaSuccess) e = mark(4);
+    if (e == cudaSuccess && two) e = launch_gbest(bv, 1, st);
+    if (e == cudaSuccess) e = mark(5);
     return e;
 }
 
-// One generation of Fig. "pseudocode" for one swarm: particle update,
-// mutation (when due), gbest, then the edge exchange and a second gbest pass
-// (both no-ops unless the first gbest pass scheduled the exchange).
-cudaError_t enqueue_generation(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
-    return enqueue_batch_generation(swarm_view(s), swarm_two_opt(s),
-                                    (s->k.flags & DPSO_FLAG_TWO_OPT) != 0, mut_iter, s->num_sms,
-                                    st);
-}
-
-// Timing mode: the same kernels as enqueue_generation with events between the
-// phases (move | mutation | gbest | 2-opt | gbest).
-cudaError_t enqueue_generation_timed(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
-    const size_t base = s->pending.size() * 6;
-    while (s->ev_pool.size() < base + 6) {
+// Timing mode: rebinds the graph's event-record nodes to kPhaseEvents fresh
+// pool events and replays it (an update of a graph exec affects only later
+// launches, so generations already enqueued keep their own events).
+cudaError_t launch_generation_timed(dpso_swarm* s, bool mut_iter, cudaStream_t st) {
+    const size_t base = s->pending.size() * kPhaseEvents;
+    while (s->ev_pool.size() < base + kPhaseEvents) {
         cudaEvent_t e;
         cudaError_t r = cudaEventCreate(&e);
         if (r != cudaSuccess) return r;
         s->ev_pool.push_back(e);
     }
-    cudaEvent_t* ev = s->ev_pool.data() + base;
-    const bool two = (s->k.flags & DPSO_FLAG_TWO_OPT) != 0;
-    const BatchView bv = swarm_view(s);
-    const TwoOptBatch tb = swarm_two_opt(s);
-    cudaError_t e = cudaEventRecord(ev[0], st);
-    if (e == cudaSuccess) e = launch_move(bv, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[1], st);
-    if (e == cudaSuccess && mut_iter) e = launch_mutation(bv, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[2], st);
-    if (e == cudaSuccess) e = launch_gbest(bv, 0, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[3], st);
-    if (e == cudaSuccess && two) e = launch_rank_cost(bv, st);
-    if (e == cudaSuccess && two) e = cudaMemsetAsync(tb.queue, 0, sizeof(unsigned int), st);
-    if (e == cudaSuccess && two) e = launch_two_opt(tb, s->num_sms, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[4], st);
-    if (e == cudaSuccess && two) e = launch_gbest(bv, 1, st);
-    if (e == cudaSuccess) e = cudaEventRecord(ev[5], st);
-    if (e == cudaSuccess) s->pending.push_back({static_cast<int>(base), mut_iter ? 1 : 0});
+    const int g = mut_iter ? 1 : 0;
+    for (int q = 0; q < kPhaseEvents; ++q) {
+        cudaError_t r =
+            cudaGraphExecEventRecordNodeSetEvent(s->exec[g], s->ev_node[g][q], s->ev_pool[base + q]);
+        if (r != cudaSuccess) return r;
+    }
+    cudaError_t e = cudaGraphLaunch(s->exec[g], st);
+    if (e == cudaSuccess) s->pending.push_back({static_cast<int>(base), g});
     return e;
 }
 
 int collect_timing(dpso_swarm* s) {
     for (const auto& pr : s->pending) {
-        cudaEvent_t* ev = s->ev_pool.data() + pr[0];
+        cudaEvent_t* ev = s->ev_pool.data() + pr[0];  // kPhaseEvents events
         float t[5];
         for (int q = 0; q < 5; ++q) CK(cudaEventElapsedTime(&t[q], ev[q], ev[q + 1]));
         const bool two = (s->k.flags & DPSO_FLAG_TWO_OPT) != 0;
@@ -246,18 +255,41 @@ int collect_timing(dpso_swarm* s) {
     return DPSO_OK;
 }
 
-int capture(dpso_swarm* s, bool mut_iter, cudaGraphExec_t* out) {
-    cudaGraph_t g = nullptr;
+// Captures the generation graph with (g = 1) or without (g = 0) mutation,
+// keeps it (its event-record nodes are rebound in timing mode) and
+// instantiates it.
+int capture(dpso_swarm* s, int g) {
+    for (cudaEvent_t& e : s->ev_cap)
+        if (!e) CK(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaGraph_t graph = nullptr;
     CK(cudaStreamBeginCapture(s->cap, cudaStreamCaptureModeRelaxed));
-    const cudaError_t e = enqueue_generation(s, mut_iter, s->cap);
-    const cudaError_t e2 = cudaStreamEndCapture(s->cap, &g);
+    const cudaError_t e = enqueue_generation(s, g == 1, s->cap, s->ev_cap);
+    const cudaError_t e2 = cudaStreamEndCapture(s->cap, &graph);
     if (e != cudaSuccess || e2 != cudaSuccess) {
-        if (g) cudaGraphDestroy(g);
+        if (graph) cudaGraphDestroy(graph);
         return DPSO_ERR_CUDA;
     }
-    const cudaError_t e3 = cudaGraphInstantiate(out, g, 0);
-    cudaGraphDestroy(g);
-    return e3 == cudaSuccess ? DPSO_OK : DPSO_ERR_CUDA;
+    s->graph[g] = graph;
+    size_t count = 0;
+    CK(cudaGraphGetNodes(graph, nullptr, &count));
+    std::vector<cudaGraphNode_t> nodes(count);
+    CK(cudaGraphGetNodes(graph, nodes.data(), &count));
+    int found = 0;
+    for (cudaGraphNode_t nd : nodes) {
+        cudaGraphNodeType type;
+        CK(cudaGraphNodeGetType(nd, &type));
+        if (type != cudaGraphNodeTypeEventRecord) continue;
+        cudaEvent_t ev = nullptr;
+        CK(cudaGraphEventRecordNodeGetEvent(nd, &ev));
+        for (int q = 0; q < kPhaseEvents; ++q)
+            if (ev == s->ev_cap[q] && !s->ev_node[g][q]) {
+                s->ev_node[g][q] = nd;
+                ++found;
+            }
+    }
+    if (found != kPhaseEvents) return DPSO_ERR_INTERNAL;
+    CK(cudaGraphInstantiate(&s->exec[g], graph, 0));
+    return DPSO_OK;
 }
 
 // Makes room for `need` history entries (the device reads the pointer from
@@ -623,7 +655,7 @@ int dpso_init(dpso_swarm** out, const int32_t* C_dev, int32_t n, const int32_t* 
 
     if (cudaStreamCreateWithFlags(&s->cap, cudaStreamNonBlocking) != cudaSuccess)
         return fail(DPSO_ERR_CUDA);
-    if ((st = capture(s, false, &s->g_plain)) || (st = capture(s, true, &s->g_mut))) return fail(st);
+    if ((st = capture(s, 0)) || (st = capture(s, 1))) return fail(st);
     *out = s;
     return DPSO_OK;
 }
@@ -643,8 +675,8 @@ int dpso_step(dpso_swarm* s, int32_t iterations, void* stream) {
     for (int it = 0; it < iterations; ++it) {
         const int t = s->t_host + 1 + it;
         const bool mut = (s->k.flags & DPSO_FLAG_MUTATION) && (t % s->k.mut_period == 0);
-        if (s->timing) CK(enqueue_generation_timed(s, mut, st));
-        else CK(cudaGraphLaunch(mut ? s->g_mut : s->g_plain, st));
+        if (s->timing) CK(launch_generation_timed(s, mut, st));
+        else CK(cudaGraphLaunch(s->exec[mut ? 1 : 0], st));
     }
     s->t_host += iterations;
     return DPSO_OK;
@@ -756,21 +788,27 @@ int dpso_set_state(dpso_swarm* s, const void* buf, size_t bytes) {
     CK(cudaStreamSynchronize(s->last));
     int st = ensure_history(s, std::max(h.t, 1));
     if (st) return st;
+    // every copy is ordered on the swarm's own stream, which is then waited
+    // for: a copy from pageable memory may return before its transfer lands,
+    // and the caller's next launch may be on a non-blocking stream
+    cudaStream_t st0 = s->last;
     const unsigned char* o = static_cast<const unsigned char*>(buf) + sizeof(h);
     const size_t row = n * sizeof(uint16_t), pitch = s->k.ldn * sizeof(uint16_t);
     for (uint16_t* A : {s->X, s->V, s->P}) {
-        CK(cudaMemcpy2D(A, pitch, o, row, row, S, cudaMemcpyHostToDevice));
+        CK(cudaMemcpy2DAsync(A, pitch, o, row, row, S, cudaMemcpyHostToDevice, st0));
         o += row * S;
     }
-    CK(cudaMemcpy(s->G, o, row, cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(s->G, o, row, cudaMemcpyHostToDevice, st0));
     o += row;
-    CK(cudaMemcpy(s->F, o, S * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(s->F, o, S * sizeof(int64_t), cudaMemcpyHostToDevice, st0));
     o += S * sizeof(int64_t);
-    CK(cudaMemcpy(s->PF, o, S * sizeof(int64_t), cudaMemcpyHostToDevice));
+    CK(cudaMemcpyAsync(s->PF, o, S * sizeof(int64_t), cudaMemcpyHostToDevice, st0));
     o += S * sizeof(int64_t);
-    if (h.t > 0) CK(cudaMemcpy(s->hist, o, sizeof(int64_t) * h.t, cudaMemcpyHostToDevice));
+    if (h.t > 0)
+        CK(cudaMemcpyAsync(s->hist, o, sizeof(int64_t) * h.t, cudaMemcpyHostToDevice, st0));
     Ctl c;
-    CK(cudaMemcpy(&c, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost));
+    CK(cudaMemcpyAsync(&c, s->ctl, sizeof(Ctl), cudaMemcpyDeviceToHost, st0));
+    CK(cudaStreamSynchronize(st0));
     c.gf = h.gf;
     c.gf_start = h.gf;
     c.t = h.t;
@@ -783,10 +821,8 @@ int dpso_set_state(dpso_swarm* s, const void* buf, size_t bytes) {
     c.pairs = h.pairs;
     c.moves = h.moves;
     c.runs = h.runs;
-    CK(cudaMemcpy(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice));
-    // copies from pageable memory may return before their transfer lands;
-    // finish them before the caller's (possibly non-blocking) stream runs on
-    CK(cudaDeviceSynchronize());
+    CK(cudaMemcpyAsync(s->ctl, &c, sizeof(Ctl), cudaMemcpyHostToDevice, st0));
+    CK(cudaStreamSynchronize(st0));
     s->t_host = h.t;
     return DPSO_OK;
 }

@@ -46,3 +46,23 @@ def assert_same_state(gpu_state, ref: "oracle.Swarm", what=""):
     assert gpu_state["gf"] == rs["gf"], (what, gpu_state["gf"], rs["gf"])
     assert gpu_state["t"] == rs["t"], (what, gpu_state["t"], rs["t"])
     assert np.array_equal(gpu_state["history"], ref.history()), what
+
+
+def checkpoint_with_flags(blob: bytes, flags: int) -> bytes:
+    """The checkpoint `blob` with its parameter block's flags replaced, so it
+    can be loaded into a swarm created with those flags (dpso_set_state
+    accepts only a checkpoint taken with the swarm's own parameters)."""
+    import ctypes
+    import struct
+    off = dpso._HDR_SIZE - ctypes.sizeof(dpso.dpso_params) + dpso.dpso_params.flags.offset
+    out = bytearray(blob)
+    struct.pack_into("<i", out, off, flags)
+    return bytes(out)
+
+
+def host_threads() -> int:
+    import os
+    try:
+        return max(1, len(os.sched_getaffinity(0)))
+    except AttributeError:
+        return max(1, os.cpu_count() or 1)

@@ -66,8 +66,32 @@ def test_reference_arm_line(monkeypatch):
                          "--workload", "tiny"])
     line = json.loads(buf.getvalue())
     assert rc == 0 and line["impl"] == "reference" and line["value"] > 0
-    assert line["cpu_baseline"]["kind"] == "oracle" and line["cpu_baseline"]["cores"] == 1
+    assert line["cpu_baseline"]["kind"] == "oracle"
+    assert line["cpu_baseline"]["cores"] == bench.cpu_cores()
     assert line["e2e"]["h2d_bytes_per_step"] == 0
+    # the workload's config, plus the oracle sample's real swarm size
+    assert line["config"]["workload"] == "tiny-30vp-32p" and line["config"]["swarm"] == 32
+    assert line["config"]["sample_swarm"] == bench.reference_swarm(30, bench.cpu_cores())
+
+
+def test_default_workload_is_the_bridge():
+    import argparse
+    assert bench.DEFAULT_STEPS["bridge"] * 2.5 < 120      # about a minute of timed work
+    # parse the defaults without running anything
+    captured = {}
+
+    def fake_line(args):
+        captured.update(vars(args))
+        return None
+    orig = bench.gpu_line
+    bench.gpu_line = fake_line
+    try:
+        bench.main([])
+    finally:
+        bench.gpu_line = orig
+    assert captured["workload"] == "bridge" and captured["steps"] == 20
+    assert captured["warmup"] >= 3
+    assert isinstance(argparse.Namespace(**captured), argparse.Namespace)
 
 
 def _shard_rank(rank, world, port, out):
@@ -101,11 +125,13 @@ def test_instance_sharding_covers_every_instance_once():
 
 
 def test_oracle_sample_is_bounded_by_instance_size():
-    # the bridge-sized oracle sample stays a few particles and one generation
-    assert bench.cpu_sample_shape(400) == (16, 10)
-    assert bench.cpu_sample_shape(400, node_swap=True) == (16, 4)
-    s, g = bench.cpu_sample_shape(1992)
-    assert s * g <= 4
+    # the bridge-sized oracle sample is one generation of one particle per
+    # host thread (each particle's exchange on its own thread)
+    assert bench.cpu_sample_shape(400, 16) == (128, 4)
+    assert bench.cpu_sample_shape(400, 16, node_swap=True) == (128, 2)
+    s, g = bench.cpu_sample_shape(1992, 16)
+    assert (s, g) == (16, 1)
+    assert bench.reference_swarm(1992, 16) == 16
 
 
 def test_clock_samples_are_kept_only_inside_the_timed_window(tmp_path):

@@ -779,3 +779,106 @@ def test_fitness_sums_past_the_int32_range(oracle_mod):
     x = np.arange(n, dtype=np.uint16)
     C[5, 6] = C[6, 5] = 7
     assert oracle_mod.fitness(C, x) == (n - 1) * K + 7
+
+
+# ------------------------------------------------------------- snapshot replay
+
+IMPORT_CASES = {
+    "default": {},
+    "w_half": dict(w=0.5),
+    "w_zero": dict(w=0.0, phi1=0.7, phi2=0.9),
+    "trigger1": dict(trigger=1),
+    "period2_swaps5": dict(mut_period=2, mut_swaps=5, det_frac_pct=40),
+    "stall": dict(stall_limit=3),
+    "node_swap": dict(flags=7 | 8),
+    "max_moves": dict(max_moves=2),
+}
+
+
+@pytest.mark.parametrize("case", list(IMPORT_CASES))
+def test_import_continues_an_uninterrupted_run(oracle_mod, case):
+    """A state exported at generation k and imported into a fresh swarm
+    continues exactly as the run it came from (every array, the history, the
+    loop state and the exchange counters), for every generation kind."""
+    inst = inputs.random_instance(33, 3, 61)
+    C, _ = oracle_mod.cost_matrix(inst.xyz, inst.boxes)
+    kw = IMPORT_CASES[case]
+    for k in (0, 1, 2, 3, 7):
+        a = oracle_mod.Swarm(C, inst.tags, swarm=21, seed=17, **kw)
+        a.run(k)
+        b = oracle_mod.Swarm(C, inst.tags, swarm=21, seed=17, **kw)
+        b.load_state(a.state())
+        for _ in range(6):
+            a.iterate()
+            b.iterate()
+            sa, sb = a.state(), b.state()
+            for key in sa:
+                assert np.array_equal(sa[key], sb[key]), (case, k, key, sa["t"])
+
+
+def test_import_stores_minimal_velocities(oracle_mod):
+    """An imported velocity becomes the subtraction's list for its
+    permutation: n - cycles transpositions (Sec. 3.1: x1 + (x2 - x1) = x2),
+    and with w = 1 the next position is that permutation applied after the
+    two new terms' transpositions: x' = V' o x for the new velocity V'."""
+    inst = inputs.random_instance(29, 2, 62)
+    C, _ = oracle_mod.cost_matrix(inst.xyz, inst.boxes)
+    sw = oracle_mod.Swarm(C, inst.tags, swarm=12, seed=3, flags=0)
+    st = sw.state()
+    rng = np.random.default_rng(11)
+    ident = np.arange(29, dtype=np.uint16)
+    st["V"] = np.stack([rng.permutation(29) for _ in range(12)]).astype(np.uint16)
+    sw.load_state(st)
+    for p in range(12):
+        assert sw.vel_len(p) == 29 - _label_cycles(st["V"][p], ident)
+    x0 = sw.state()["X"]
+    sw.move(1)
+    after = sw.state()
+    for p in range(12):
+        assert np.array_equal(after["V"][p][x0[p].astype(int)], after["X"][p])
+
+
+def test_import_rejects_non_permutations(oracle_mod):
+    inst = inputs.random_instance(15, 1, 63)
+    C, _ = oracle_mod.cost_matrix(inst.xyz, inst.boxes)
+    sw = oracle_mod.Swarm(C, inst.tags, swarm=6, seed=2)
+    sw.run(2)
+    good = sw.state()
+    for key in ("X", "P", "V"):
+        bad = {k: (v.copy() if isinstance(v, np.ndarray) else v) for k, v in good.items()}
+        bad[key][3, 4] = bad[key][3, 5]
+        with pytest.raises(ValueError):
+            sw.load_state(bad)
+    bad = dict(good, G=np.zeros(15, np.uint16))
+    with pytest.raises(ValueError):
+        sw.load_state(bad)
+    after = sw.state()                    # a rejected import leaves the swarm alone
+    for key in good:
+        assert np.array_equal(good[key], after[key]), key
+
+
+def test_threaded_exchange_equals_serial_generation(oracle_mod):
+    """The generation split around the exchange, with the exchange run by
+    several threads on disjoint particles, equals iterate()."""
+    inst = inputs.random_instance(48, 3, 64)
+    C, _ = oracle_mod.cost_matrix(inst.xyz, inst.boxes)
+    a = oracle_mod.Swarm(C, inst.tags, swarm=30, seed=8)
+    b = oracle_mod.Swarm(C, inst.tags, swarm=30, seed=8)
+    ran = 0
+    for _ in range(8):
+        a.iterate()
+        ran += b.iterate_threaded(threads=4)
+        sa, sb = a.state(), b.state()
+        for key in sa:
+            assert np.array_equal(sa[key], sb[key]), (key, sa["t"])
+    assert ran > 0
+    # with a sample only those particles are exchanged and the generation stays open
+    c = oracle_mod.Swarm(C, inst.tags, swarm=30, seed=8)
+    c.load_state(a.state())
+    a.iterate()
+    if c.iterate_threaded(threads=3, sample=[2, 17, 29]):
+        sa, sc = a.state(), c.state()
+        for p in (2, 17, 29):
+            assert np.array_equal(sa["X"][p], sc["X"][p]) and sa["F"][p] == sc["F"][p]
+        with pytest.raises(RuntimeError):
+            c.iterate_begin()             # still open

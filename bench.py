@@ -35,6 +35,7 @@ fitness_roofline  the tour-fitness kernel (Eq. min) over the swarm's tours:
 from __future__ import annotations
 
 import argparse
+import dataclasses
 import hashlib
 import json
 import os
@@ -377,6 +378,8 @@ def gpu_line(args):
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
     inst = workload(args.workload)
+    if args.swarm:                 # a smaller swarm of the same instance (profiling)
+        inst = dataclasses.replace(inst, swarm=args.swarm)
     seed = inst.seed + rank        # independent replica per rank
     S, n = inst.swarm, inst.n
     stream = torch.cuda.current_stream()
@@ -851,6 +854,9 @@ def main(argv=None):
     ap.add_argument("--max-active", type=int, default=16, help="serving: running requests at most")
     ap.add_argument("--exchange", default="2-opt", choices=["2-opt", "node-swap"],
                     help="edge exchange of the swarm workloads")
+    ap.add_argument("--swarm", type=int, default=0,
+                    help="bridge/facade/tiny: particles instead of the workload's (small "
+                         "profiling cases; the bench line then names that swarm)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
     args = ap.parse_args(argv)

@@ -27,13 +27,20 @@
 //    first group holding it, with selects only (no divergent branch in the
 //    column loop).  Subtracting C[x_i][x_i+1] gives a candidate (delta, i,
 //    group) as a packed 64-bit key; the warps of a tile fold theirs per row.
-//  * Row cache: each row's smallest key survives from pass to pass.  A move
-//    that reverses positions a+1..b changes the deltas of rows a..b, and of
-//    rows below a only in columns a..b, so the next pass re-evaluates the
-//    tiles of rows a..b in full, the tiles below a only in the groups that
-//    cover a..b (in full where a row's cached minimum lies in them), and
-//    skips the tiles past b.  The pass's move is the smallest cached key; its
-//    exact column and the two new edge costs are read from C.
+//  * Row cache: each row's smallest improving key (delta < 0; else none)
+//    survives from pass to pass.  A move that reverses positions a+1..b
+//    changes the deltas of rows a..b, and of rows below a only in columns
+//    a..b; rows past b keep theirs.  The next pass stages only the rows
+//    C[x_a..x_b+1] of the reversed segment, in segment tiles starting at a:
+//    each evaluates its own rows over every column and, since C is
+//    symmetric (C[x_i][x_j] = C[x_j][x_i]), every row i < a over its columns
+//    j in the tile, with one j per lane reading the staged rows C[x_j],
+//    C[x_j+1] at x_i, x_i+1 (the same two gathers per pair, conflict-free;
+//    the minimum over j is taken across lanes, only for groups where some
+//    lane holds an improving pair).  Rows below a whose cached move lay in a
+//    group touching a..b are evaluated afresh in full, in the grid tiles that
+//    hold them.  The pass's move is the smallest cached key; its exact column
+//    and the two new edge costs are read from C.
 //  * Pairs with j = i+1 and (0, n-1) have delta = 0 for a symmetric C and
 //    never win, so only the triangle at the start of each tile is masked.
 #include <climits>
@@ -59,6 +66,9 @@ __global__ void shift_copies_kernel(const int* __restrict__ C, int ldc, int n, i
 
 }  // namespace
 
+// Tiles of a tour's fixed tile grid (rows 0..n-3 in tiles of `rows`).
+__host__ __device__ inline int grid_tiles(int n, int rows) { return (n - 2 + rows - 1) / rows; }
+
 size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages) {
     const size_t rows =
         static_cast<size_t>(stages) * (rows_per_tile + 1) * shifted_ld(n) * sizeof(int);
@@ -66,7 +76,11 @@ size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages) {
     const size_t xs = static_cast<size_t>((n + 1 + 7) / 8 * 8) * sizeof(uint16_t);
     // the row cache
     const size_t cache = static_cast<size_t>((n + 1) & ~1) * sizeof(uint64_t);
-    return rows + rec + xs + cache;
+    // the pass's need-tile bitmask (words) and list (uint16), 8-byte multiples
+    const int nt = grid_tiles(n, rows_per_tile);
+    const size_t bits = static_cast<size_t>((nt + 63) / 64 * 2) * sizeof(unsigned);
+    const size_t list = static_cast<size_t>((nt + 3) / 4 * 4) * sizeof(uint16_t);
+    return rows + rec + xs + cache + bits + list;
 }
 
 namespace {
@@ -121,8 +135,16 @@ __device__ __forceinline__ void half_sync(int grp, int half) {
 // subgroup with its own tile buffer and barrier, so a tour's passes take
 // about half as long (a shorter tail when tours need very different pass
 // counts) for the same shared memory and warps per SM as two CTAs.
+// Resident CTAs per SM the register budget is sized for: two for the
+// 16-warp shapes and for one long tour per CTA (16- and 8-row tiles, where
+// shared memory holds at most two CTAs), four for 30-row tiles, else three.
 template <int ROWS, int TPC, int TG>
-__global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 : 3))
+constexpr int tiled_min_blocks() {
+    return TG == 2 || (TPC == 1 && ROWS <= 16) ? 2 : (ROWS == 30 ? 4 : 3);
+}
+
+template <int ROWS, int TPC, int TG>
+__global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG>()))
     two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
     static_assert(TG == 1 || TPC == 1, "two tile subgroups need the whole CTA");
     constexpr int kRows = ROWS;        // positions per tile, one per lane
@@ -142,7 +164,8 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
     __shared__ unsigned long long s_best[TPC];
     __shared__ unsigned int s_next[TPC];     // tiles taken in this pass (TG = 2)
     __shared__ int s_tile[TPC * TG * 2];     // a subgroup's next tile, by parity
-    __shared__ int s_mode[TPC * TG];         // 1: the subgroup's tile is full
+    // s_part: the tour's work item, then each pass's need-tile count, then
+    // the winning column (each read after a barrier, before the next write)
     __shared__ int s_part[TPC], s_e0[TPC], s_e1[TPC], s_p[TPC];
     __shared__ long long s_pf[TPC], s_f[TPC];
     // The tour's task descriptor, its running cost and the subgroups' counts of
@@ -207,7 +230,10 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         const int xs16 = (rec2 + n + 4) * 4;    // uint16 index of x_0
         // u64 index of the row cache, after the tour (n + 1 uint16, padded)
         const int rk64 = (xs16 + (n + 1 + 7) / 8 * 8 + 3) / 4;
-        const int ntiles = (n - 2 + kRows - 1) / kRows;  // tiles start at I <= n-3
+        const int ntiles = grid_tiles(n, kRows);  // grid tiles start at I <= n-3
+        // the pass's need-tile bitmask (u32 index) and list (uint16 index)
+        const int nb32 = 2 * (rk64 + ((n + 1) & ~1));
+        const int nl16 = 2 * (nb32 + (ntiles + 63) / 64 * 2);
         const int guard = 1000 + 100 * n;
 
         // The subgroup stages the `count` cost rows of the tile starting at I:
@@ -268,17 +294,21 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
         int moves = 0, passes = 0;
         group_sync<TPC>(grp);
 
-        // Row cache: rowkey[i] is the smallest (delta, i, group) of row i over
-        // all its columns, as of the last pass that evaluated it.  A move that
-        // reverses positions pa+1..pb changes the pairs of rows pa..pb and,
-        // for rows below pa, only columns pa..pb; rows above pb keep theirs.
-        // The warps of a tile fold their keys into it with shared atomicMin.
+        // Row cache: rowkey[i] is the smallest (delta, i, column) of row i
+        // over all its columns when that delta is negative (an improving
+        // move), else ~0, as of the last pass that evaluated the row.  A move
+        // that reverses positions pa+1..pb changes the pairs of rows pa..pb
+        // and, for rows below pa, only columns pa..pb; rows above pb keep
+        // theirs.  The warps fold their keys into it with shared atomicMin.
         unsigned long long* const rowkey = reinterpret_cast<unsigned long long*>(smi) + rk64;
+        unsigned* const needbits = reinterpret_cast<unsigned*>(smi) + nb32;
+        uint16_t* const needlist = smu + nl16;
         int pa = -1, pb = -1;  // the previous move; pb < 0: evaluate every pair
         if (tid == 0) {
             s_best[grp] = ~0ull;
             s_next[grp] = 0;
         }
+        for (int w = tid; w < (ntiles + 31) / 32; w += GT) needbits[w] = 0;
         group_sync<TPC>(grp);
 
         for (;;) {
@@ -288,129 +318,216 @@ __global__ void __launch_bounds__(kThreads * TG, TG == 2 ? 2 : (ROWS == 30 ? 4 :
                 break;
             }
             const bool first = pb < 0;
-            const int tlast = first ? ntiles - 1 : min(ntiles - 1, pb / kRows);
-            // Tiles are taken from the last one down (the tiles that need every
-            // column come first); with two subgroups each takes the next one
-            // when it finishes its own (s_tile, double-buffered by tile parity,
-            // published before the subgroup barrier that the readers pass).
+            // The pass's tiles.  First pass: every grid tile, in full.  After a
+            // move (pa, pb): nseg segment tiles of rows pa.., starting at pa,
+            // whose staged rows pa..pb+1 also serve every row below pa over
+            // columns pa..pb (C is symmetric: C[x_i][x_j] = C[x_j][x_i]); then
+            // the grid tiles holding a row below pa whose cached improving
+            // move lay in a group touching pa..pb (its row is evaluated afresh
+            // in full).  Keys of the rows evaluated in full are reset first.
+            int nseg = 0;
+            if (first) {
+                for (int r = tid; r <= n - 3; r += GT) rowkey[r] = ~0ull;
+            } else {
+                nseg = (pb - pa + kRows) / kRows;
+                for (int r = tid; r <= min(pb, n - 3); r += GT) {
+                    if (r >= pa) {
+                        rowkey[r] = ~0ull;
+                    } else {
+                        const unsigned long long k = rowkey[r];
+                        const int cmc = static_cast<int>(k & 0xffffu);
+                        if (k != ~0ull && cmc + 3 >= pa && cmc <= pb) {
+                            rowkey[r] = ~0ull;
+                            atomicOr(&needbits[(r / kRows) >> 5], 1u << ((r / kRows) & 31));
+                        }
+                    }
+                }
+            }
+            group_sync<TPC>(grp);
+            if (!first && warp == 0) {
+                // compact the need bitmask into a list (one warp; at most 32
+                // words: n <= 4168 tours have at most 521 grid tiles) and clear it
+                const int nw = (ntiles + 31) / 32;
+                const unsigned bits = lane < nw ? needbits[lane] : 0u;
+                const int cnt = __popc(bits);
+                int incl = cnt;
+#pragma unroll
+                for (int o = 1; o < 32; o <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, incl, o);
+                    if (lane >= o) incl += y;
+                }
+                int pos = incl - cnt;
+                for (unsigned b = bits; b; b &= b - 1) needlist[pos++] = static_cast<uint16_t>(32 * lane + __ffs(b) - 1);
+                if (lane < nw) needbits[lane] = 0u;
+                if (lane == 31) s_part[grp] = incl;  // (the work item is no longer needed this tour)
+            }
+            group_sync<TPC>(grp);
+            const int ntot = first ? ntiles : nseg + s_part[grp];
+            // Tiles are taken in order (segment tiles first); with two
+            // subgroups each takes the next one when it finishes its own
+            // (s_tile, double-buffered by tile parity, published before the
+            // subgroup barrier that the readers pass).
             int par = 0, taken = 0;
             if (TG == 2 && wsg == 0 && lane == 0)
-                s_tile[sg * 2] = tlast - static_cast<int>(atomicAdd(&s_next[grp], 1u));
+                s_tile[sg * 2] = static_cast<int>(atomicAdd(&s_next[grp], 1u));
             for (;;) {
                 half_sync<TPC, TG>(grp, half);  // the previous tile is no longer read
                 if (s_abort[sg]) break;  // read after the barrier: the subgroup agrees
-                const int t = TG == 1 ? tlast - taken : s_tile[sg * 2 + par];
-                if (t < 0) break;
+                const int t = TG == 1 ? taken : s_tile[sg * 2 + par];
+                if (t >= ntot) break;
                 ++taken;
-                const int I = t * kRows;
-                const int count = min(kStaged, n - 1 - I);
+                const bool seg = !first && t < nseg;
+                const int I = seg ? pa + t * kRows : (first ? t : needlist[t - nseg]) * kRows;
+                // staged rows I..I+count-1; rows evaluated in full I..rlast
+                const int count = seg ? min(kStaged, pb + 2 - I) : min(kStaged, n - 1 - I);
+                const int rlast = seg ? min(min(I + kRows - 1, pb), n - 3)
+                                      : (first ? n - 3 : min(pa - 1, n - 3));
                 stage(I, count);
-                const int i = I + lane;
-                const bool row_ok = lane < kRows && i <= n - 3;
                 if (wsg == 0) {
-                    // the tile's mode: rows pa..pb (or the first pass) need every
-                    // column; rows below pa only pa..pb, unless a row's cached
-                    // minimum sits in a group that touches pa..pb.  A full tile
-                    // starts its rows' keys afresh.  Both happen before the
-                    // barrier arrival that the other warps acquire.
-                    bool full = first || (I <= pb && I + kRows - 1 >= pa);
-                    if (!full) {
-                        bool need = false;
-                        if (row_ok) {
-                            const int cmc = static_cast<int>(rowkey[i] & 0xffffu);
-                            need = cmc + 3 >= pa && cmc <= pb;
-                        }
-                        full = __any_sync(0xffffffffu, need);
-                    }
-                    if (full && row_ok) rowkey[i] = ~0ull;
-                    if (lane == 0) s_mode[sg] = full ? 1 : 0;
                     __syncwarp();
                     if (lane == 0) mbar_expect(mbar, static_cast<unsigned>(count) * row_bytes);
                 }
                 stage_wait();
-                const bool full = s_mode[sg] != 0;
                 // the row this lane evaluates (lanes past the tile height idle
                 // on a valid row unless the tile splits the warp); byte offsets
                 // of its two staged rows (row start plus its 0..3 word shift)
                 const int lrow = SPLIT > 1 ? (lane & (kRows - 1)) : min(lane, kRows - 1);
                 const int part = SPLIT > 1 ? lane / kRows : 0;
                 const int ie = I + lrow;
-                const bool eval_ok = (SPLIT > 1 || lane < kRows) && ie <= n - 3;
+                const bool eval_ok = (SPLIT > 1 || lane < kRows) && ie <= rlast;
                 const int ra = lrow, rb1 = lrow + 1;
                 const int p1 = half * buf_words + ra * ldq + ((ra >> 3) & 3);
                 const int p2 = half * buf_words + rb1 * ldq + ((rb1 >> 3) & 3);
                 const char* const r1 = reinterpret_cast<const char*>(smi + p1);
                 const char* const r2 = reinterpret_cast<const char*>(smi + p2);
-                // columns in groups of four from I+2 (partial tiles: the groups
-                // that hold pa..pb, on the same grid), contiguous per warp; the
-                // records past n are padding
-                const int cbeg = I + 2;
-                int cstart = cbeg, cstop = n;
-                if (!full) {
-                    cstart = cbeg + ((max(pa, cbeg) - cbeg) & ~3);
-                    cstop = min(n, pb + 1);
-                }
-                const int ngroups = cstop > cstart ? (cstop - cstart + 3) >> 2 : 0;
-                const int g0 = (ngroups * wsg) / WSG, g1 = (ngroups * (wsg + 1)) / WSG;
-                if (wsg == 0) {
-                    // pairs (i, j), i+2 <= j <= n-1, (i, j) != (0, n-1), in the
-                    // columns evaluated: cstart .. E-1
-                    const int E = min(cstart + 4 * ngroups, n);
-                    int cnt = row_ok ? max(0, E - max(cstart, i + 2)) : 0;
-                    cnt -= (i == 0 && E == n && cnt > 0) ? 1 : 0;
-                    const unsigned tc = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(cnt));
-                    if (lane == 0) s_evals[sg] += tc;
-                }
-                // this lane group's share of the warp's groups
-                int h0 = g0, h1 = g1;
-                if constexpr (SPLIT > 1) {
-                    h0 = g0 + ((g1 - g0) * part) / SPLIT;
-                    h1 = g0 + ((g1 - g0) * (part + 1)) / SPLIT;
-                }
-                // first valid column of this lane's row (rows past n-3 have none)
-                const int lim = eval_ok ? ie + 2 : INT_MAX;
-                int m = INT_MAX, cm = 0;
-                int c = cstart + 4 * h0;
-                const int cend = cstart + 4 * h1;
-                int q = h0 < h1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
-                const int4* rp = smi4 + ((rec2 + c) >> 1);   // records c .. c+3
                 auto at = [](const char* row, int off) {
                     return *reinterpret_cast<const int*>(row + off);
                 };
-                auto group = [&](bool masked) {
-                    const int4 ra4 = rp[0], rb4 = rp[1];
-                    int v0 = at(r1, q) + at(r2, ra4.x) + ra4.y;
-                    int v1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w;
-                    int v2 = at(r1, ra4.z) + at(r2, rb4.x) + rb4.y;
-                    int v3 = at(r1, rb4.x) + at(r2, rb4.z) + rb4.w;
-                    if (masked) {
-                        v0 = c >= lim ? v0 : INT_MAX;
-                        v1 = c + 1 >= lim ? v1 : INT_MAX;
-                        v2 = c + 2 >= lim ? v2 : INT_MAX;
-                        v3 = c + 3 >= lim ? v3 : INT_MAX;
+                // (a) the tile's rows over every column: groups of four from
+                // the even column at or below I+2 (records are read in pairs),
+                // contiguous per warp; the records past n are padding
+                const int cstart = (I + 2) & ~1;
+                const int ngroups = (n - cstart + 3) >> 2;
+                const int g0 = (ngroups * wsg) / WSG, g1 = (ngroups * (wsg + 1)) / WSG;
+                if (wsg == 0) {
+                    // pairs (i, j), i+2 <= j <= n-1, (i, j) != (0, n-1), of the rows
+                    // evaluated in full, and of the rows below pa against the
+                    // segment's columns (segment tiles)
+                    const bool row_ok = lane < kRows && I + lane <= rlast;
+                    int cnt = row_ok ? n - (I + lane) - 2 : 0;
+                    cnt -= (I + lane == 0 && cnt > 0) ? 1 : 0;
+                    if (seg && pa > 0 && lane < kRows && I + lane <= pb) {
+                        const int j = I + lane;
+                        cnt += pa - (j == pa ? 1 : 0) - (j == n - 1 ? 1 : 0);
                     }
-                    const int mv = min(min(v0, v1), min(v2, v3));
-                    cm = mv < m ? c : cm;  // first group holding the lane minimum
-                    m = min(m, mv);
-                    q = rb4.z;
-                    c += 4;
-                    rp += 2;
-                };
-                // groups starting below I+33 hold the diagonal triangle
-                const int cmask = min(cend, I + kStaged);
-                while (c < cmask) group(true);
-                while (c < cend) group(false);
-                unsigned long long key = m != INT_MAX && eval_ok
-                                             ? pack_key(m + smi2[rec2 + ie].y, ie, cm)
-                                             : ~0ull;
-                if constexpr (SPLIT > 1) {  // the lane groups sharing a row
-                    key = min(key, __shfl_xor_sync(0xffffffffu, key, 16));
-                    if constexpr (SPLIT == 4) key = min(key, __shfl_xor_sync(0xffffffffu, key, 8));
+                    const unsigned tc = __reduce_add_sync(0xffffffffu, static_cast<unsigned>(cnt));
+                    if (lane == 0) s_evals[sg] += tc;
                 }
-                if (part == 0 && key != ~0ull) atomicMin(&rowkey[ie], key);
+                {
+                    // this lane group's share of the warp's groups
+                    int h0 = g0, h1 = g1;
+                    if constexpr (SPLIT > 1) {
+                        h0 = g0 + ((g1 - g0) * part) / SPLIT;
+                        h1 = g0 + ((g1 - g0) * (part + 1)) / SPLIT;
+                    }
+                    // first valid column of this lane's row (rows past rlast have none)
+                    const int lim = eval_ok ? ie + 2 : INT_MAX;
+                    int m = INT_MAX, cm = 0;
+                    int c = cstart + 4 * h0;
+                    const int cend = cstart + 4 * h1;
+                    int q = h0 < h1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
+                    const int4* rp = smi4 + ((rec2 + c) >> 1);   // records c .. c+3
+                    auto group = [&](bool masked) {
+                        const int4 ra4 = rp[0], rb4 = rp[1];
+                        int v0 = at(r1, q) + at(r2, ra4.x) + ra4.y;
+                        int v1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w;
+                        int v2 = at(r1, ra4.z) + at(r2, rb4.x) + rb4.y;
+                        int v3 = at(r1, rb4.x) + at(r2, rb4.z) + rb4.w;
+                        if (masked) {
+                            v0 = c >= lim ? v0 : INT_MAX;
+                            v1 = c + 1 >= lim ? v1 : INT_MAX;
+                            v2 = c + 2 >= lim ? v2 : INT_MAX;
+                            v3 = c + 3 >= lim ? v3 : INT_MAX;
+                        }
+                        const int mv = min(min(v0, v1), min(v2, v3));
+                        cm = mv < m ? c : cm;  // first group holding the lane minimum
+                        m = min(m, mv);
+                        q = rb4.z;
+                        c += 4;
+                        rp += 2;
+                    };
+                    // groups starting below I+kStaged+1 hold the diagonal triangle
+                    const int cmask = min(cend, I + kStaged + 1);
+                    while (c < cmask) group(true);
+                    // two groups at a time: sixteen gathers in flight
+                    while (c + 4 < cend) {
+                        const int4 ra4 = rp[0], rb4 = rp[1], rc4 = rp[2], rd4 = rp[3];
+                        const int v0 = at(r1, q) + at(r2, ra4.x) + ra4.y;
+                        const int v1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w;
+                        const int v2 = at(r1, ra4.z) + at(r2, rb4.x) + rb4.y;
+                        const int v3 = at(r1, rb4.x) + at(r2, rb4.z) + rb4.w;
+                        const int v4 = at(r1, rb4.z) + at(r2, rc4.x) + rc4.y;
+                        const int v5 = at(r1, rc4.x) + at(r2, rc4.z) + rc4.w;
+                        const int v6 = at(r1, rc4.z) + at(r2, rd4.x) + rd4.y;
+                        const int v7 = at(r1, rd4.x) + at(r2, rd4.z) + rd4.w;
+                        const int ma = min(min(v0, v1), min(v2, v3));
+                        const int mb = min(min(v4, v5), min(v6, v7));
+                        cm = ma < m ? c : cm;
+                        m = min(m, ma);
+                        cm = mb < m ? c + 4 : cm;
+                        m = min(m, mb);
+                        q = rd4.z;
+                        c += 8;
+                        rp += 4;
+                    }
+                    if (c < cend) group(false);
+                    // only improving moves enter the cache (m + the row's own
+                    // edge term < 0; no overflow: m <= 2^31 - 1 - 2^29 on a valid column)
+                    const int dl = m != INT_MAX ? m + smi2[rec2 + ie].y : 0;
+                    unsigned long long key = eval_ok && dl < 0 ? pack_key(dl, ie, cm) : ~0ull;
+                    if constexpr (SPLIT > 1) {  // the lane groups sharing a row
+                        key = min(key, __shfl_xor_sync(0xffffffffu, key, 16));
+                        if constexpr (SPLIT == 4) key = min(key, __shfl_xor_sync(0xffffffffu, key, 8));
+                    }
+                    if (part == 0 && key != ~0ull) atomicMin(&rowkey[ie], key);
+                }
+                if (seg && pa > 0) {
+                    // (b) rows i < pa against this tile's segment columns
+                    // j = I + r, one row i per lane, r over the tile:
+                    //   delta(i, j) = C[x_j][x_i] + C[x_j+1][x_i+1] - C[x_i][x_i+1]
+                    //                 - C[x_j][x_j+1]
+                    // read from the staged rows r, r + 1 (their bases are the
+                    // same on every lane), the lane keeping its smallest
+                    // negative delta and first r.  The pairs (pa - 1, pa) and
+                    // (0, n - 1) are not 2-opt moves; their delta is exactly 0
+                    // for a symmetric C, so they never enter the cache.
+                    const int jn = min(kRows, pb - I + 1);
+                    const int* const tb = smi + half * buf_words;
+                    const int nblk = (pa + 31) >> 5;
+                    for (int blk = wsg; blk < nblk; blk += WSG) {
+                        const int i = (blk << 5) + lane;
+                        const int ic = min(i, pa - 1);  // lanes past pa: a valid row, not kept
+                        const int qi = smi2[rec2 + (ic > 0 ? ic - 1 : n - 1)].x;  // 4 x_i
+                        const int2 ri = smi2[rec2 + ic];  // {4 x_i+1, -C[x_i][x_i+1]}
+                        int best = 0, br = 0;
+#pragma unroll
+                        for (int r = 0; r < kRows; ++r) {
+                            if (r < jn) {
+                                const char* const ra_ =
+                                    reinterpret_cast<const char*>(tb + r * ldq + ((r >> 3) & 3));
+                                const char* const rb_ = reinterpret_cast<const char*>(
+                                    tb + (r + 1) * ldq + (((r + 1) >> 3) & 3));
+                                const int d = at(ra_, qi) + at(rb_, ri.x) + ri.y +
+                                              smi2[rec2 + I + r].y;
+                                br = d < best ? r : br;
+                                best = min(best, d);
+                            }
+                        }
+                        if (i < pa && best < 0) atomicMin(&rowkey[i], pack_key(best, i, I + br));
+                    }
+                }
                 if (TG == 2 && wsg == 0 && lane == 0)
-                    s_tile[sg * 2 + (par ^ 1)] =
-                        tlast - static_cast<int>(atomicAdd(&s_next[grp], 1u));
+                    s_tile[sg * 2 + (par ^ 1)] = static_cast<int>(atomicAdd(&s_next[grp], 1u));
                 par ^= 1;
             }
             ++passes;
@@ -551,12 +668,12 @@ cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int tg, int num_sms, cuda
 
 // Resident CTAs per SM for a shape: shared memory (228 KB per SM; per CTA
 // 1 KB reserved by the system and under 1 KB of the kernel's static shared
-// variables) against registers (256-thread CTAs: 64 per thread at R = 30,
-// else 80; 512-thread CTAs: 64).
+// variables) against the register budget of tiled_min_blocks.
 int two_opt_tiled_ctas(int n, int rows, int tpc, int tg) {
     const int by_smem =
         static_cast<int>((228 * 1024) / (group_bytes(n, rows, tg) * tpc + 2048));
-    return min(by_smem, tg == 2 ? 2 : (rows == 30 ? 4 : 3));
+    const int by_regs = tg == 2 || (tpc == 1 && rows <= 16) ? 2 : (rows == 30 ? 4 : 3);
+    return min(by_smem, by_regs);
 }
 
 // Default launch shape for tours of n viewpoints, from sweeps on GB300 of
@@ -594,19 +711,20 @@ int two_opt_tiled_tpc(int n, int rows) {
 }
 
 // The launch shape used when none is pinned.  Long tours whose tallest
-// fitting tile has 16 rows or fewer take 8-row tiles with two tours per CTA
-// when those fit and the launch has at least two tours per SM: with the warps
-// split over column ranges, two tours in flight per SM beat one (2.17 s
-// against 2.49 s per steady-state generation of 4096 tours at n = 1992); with
-// fewer tours, pairing them would leave SMs idle.
+// fitting tile has 16 rows or fewer take 8-row tiles, one tour per CTA, when
+// two such CTAs fit on an SM and the launch has at least two tours per SM:
+// two tours in flight per SM, each with eight warps (2.34 s against 2.76 s
+// with two 4-warp tours per CTA and 3.07 s with 16-row tiles, per
+// steady-state generation of 4096 tours at n = 1992); with fewer tours the
+// tallest tile is kept.
 void two_opt_default_shape(int n, int count, int num_sms, int* rows, int* tpc, int* tg) {
     *rows = two_opt_tiled_rows(n);
     *tpc = *rows > 0 ? two_opt_tiled_tpc(n, *rows) : 0;
     *tg = *rows > 0 ? two_opt_tiled_tg(n, *rows, *tpc) : 0;
     if (*rows > 0 && *rows <= 16 && n > 256 && count >= 2 * num_sms &&
-        two_opt_tiled_fits(n, 8, 2, 1)) {
+        two_opt_tiled_fits(n, 8, 1, 1) && two_opt_tiled_ctas(n, 8, 1, 1) >= 2) {
         *rows = 8;
-        *tpc = 2;
+        *tpc = 1;
         *tg = 1;
     }
 }
@@ -618,7 +736,8 @@ cudaError_t build_shifted_copies(const int* C, int ldc, int n, int* Cs, cudaStre
 }
 
 bool two_opt_tiled_fits(int n, int rows, int tpc, int tg) {
-    return n >= 3 && n <= 65535 &&
+    // (one warp compacts the need-tile bitmask: at most 32 words of grid tiles)
+    return n >= 3 && n <= 65535 && grid_tiles(n, rows > 0 ? rows : 1) <= 1024 &&
            (rows == 32 || rows == 30 || rows == 24 || rows == 16 || rows == 8) &&
            (tpc == 1 || tpc == 2 || tpc == 4) && (tg == 1 || (tg == 2 && tpc == 1)) &&
            group_bytes(n, rows, tg) * tpc <= 220 * 1024;

@@ -143,10 +143,10 @@ def test_default_two_opt_shapes(libpath):
     shape = dpso.dpso_two_opt_default_shape
     assert shape(200, 1024, 152) == (32, 2, 1)       # short tours: two per CTA
     assert shape(400, 1024, 152) == (32, 1, 2)       # the facade: two tiles in flight
-    assert shape(1992, 4096, 152) == (8, 2, 1)       # the bridge: 8-row tiles, two tours
+    assert shape(1992, 4096, 152) == (8, 1, 1)       # the bridge: 8-row tiles, two CTAs per SM
     assert shape(1992, 152, 152) == (16, 1, 1)       # too few tours to pair them
     assert shape(1992, 303, 152) == (16, 1, 1)
-    assert shape(1992, 304, 152) == (8, 2, 1)
+    assert shape(1992, 304, 152) == (8, 1, 1)
     assert shape(2600, 4096, 152)[0] == 16           # two 8-row tours no longer fit
     assert shape(6600, 10, 152) == (0, 0, 0)         # beyond the tiled kernel
     L = dpso.lib()

@@ -491,7 +491,54 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                     }
                     if (part == 0 && key != ~0ull) atomicMin(&rowkey[ie], key);
                 }
-                if (seg && pa > 0) {
+                if (SPLIT == 1 && seg && pa > 0) {
+                    // (b) rows i < pa against this tile's segment columns
+                    // j = I + lane, one column j per lane (its staged rows
+                    // C[x_j], C[x_j+1], read at x_i, x_i+1: the same column on
+                    // every lane, so conflict-free), rows i in groups of four,
+                    // contiguous per warp:
+                    //   delta(i, j) = C[x_j][x_i] + C[x_j+1][x_i+1] - C[x_i][x_i+1]
+                    //                 - C[x_j][x_j+1],
+                    // each row's minimum over the lanes by one warp reduction; a
+                    // negative one goes to the cache with its first j.  The pairs
+                    // (pa - 1, pa) and (0, n - 1) are not 2-opt moves; their delta
+                    // is exactly 0 for a symmetric C, so they never enter it.
+                    const int j = I + lane;
+                    const bool jok = lane < kRows && j <= pb;
+                    const int tj = jok ? smi2[rec2 + j].y : 0;
+                    const int ngb = (pa + 3) >> 2;
+                    const int b0 = (ngb * wsg) / WSG, b1 = (ngb * (wsg + 1)) / WSG;
+                    int q = b0 < b1 ? smi2[rec2 + (b0 > 0 ? 4 * b0 - 1 : n - 1)].x : 0;  // 4 x_i
+                    const int4* rq = smi4 + ((rec2 + 4 * b0) >> 1);
+                    for (int gi = b0; gi < b1; ++gi) {
+                        const int i0 = 4 * gi;
+                        const int4 ra4 = rq[0], rb4 = rq[1];
+                        rq += 2;
+                        int d0 = at(r1, q) + at(r2, ra4.x) + ra4.y + tj;
+                        int d1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w + tj;
+                        int d2 = at(r1, ra4.z) + at(r2, rb4.x) + rb4.y + tj;
+                        int d3 = at(r1, rb4.x) + at(r2, rb4.z) + rb4.w + tj;
+                        q = rb4.z;
+                        d0 = jok ? d0 : INT_MAX;
+                        d1 = jok && i0 + 1 < pa ? d1 : INT_MAX;
+                        d2 = jok && i0 + 2 < pa ? d2 : INT_MAX;
+                        d3 = jok && i0 + 3 < pa ? d3 : INT_MAX;
+                        const int m0 = __reduce_min_sync(0xffffffffu, d0);
+                        const int m1 = __reduce_min_sync(0xffffffffu, d1);
+                        const int m2 = __reduce_min_sync(0xffffffffu, d2);
+                        const int m3 = __reduce_min_sync(0xffffffffu, d3);
+                        if (min(min(m0, m1), min(m2, m3)) < 0) {
+                            const int dd[4] = {d0, d1, d2, d3}, mmv[4] = {m0, m1, m2, m3};
+#pragma unroll
+                            for (int k = 0; k < 4; ++k) {
+                                const unsigned bal = __ballot_sync(0xffffffffu, dd[k] == mmv[k]);
+                                if (mmv[k] < 0 && lane == __ffs(bal) - 1)
+                                    atomicMin(&rowkey[i0 + k], pack_key(mmv[k], i0 + k, j));
+                            }
+                        }
+                    }
+                }
+                if (SPLIT > 1 && seg && pa > 0) {
                     // (b) rows i < pa against this tile's segment columns
                     // j = I + r, one row i per lane, r over the tile:
                     //   delta(i, j) = C[x_j][x_i] + C[x_j+1][x_i+1] - C[x_i][x_i+1]

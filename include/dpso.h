@@ -173,21 +173,30 @@ int dpso_two_opt(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t c
 
 /*
  * dpso_two_opt without any device allocation (the paper has no counterpart;
- * this is a deployment variant).  Same arguments, validation, results and
- * synchronisation as dpso_two_opt.  Its scratch -- error word, work queue,
- * totals, the task descriptor and per-tour pass / move counts -- lives in one
- * fixed 128 KiB device
- * array inside the library (held by every GPU that loads it, until exit)
- * instead of being allocated per call; it calls no allocating routine.
+ * this is a deployment variant).  Same arguments, the same tours, costs,
+ * pair and move counts, and the same synchronisation as dpso_two_opt, but it
+ * always runs the general (untiled) 2-opt kernel, which is slower for tours
+ * the tiled kernel takes (n <= 4168): the tiled kernel reads four row-shifted
+ * copies of the cost matrix that would have to be allocated.  Its scratch --
+ * error word, work queue, totals, the task descriptor and per-tour pass /
+ * move counts -- lives in one fixed 128 KiB device array inside the library
+ * (held by every GPU that loads it, until exit) instead of being allocated
+ * per call; it calls no allocating routine.
  * For callers that must not allocate device memory while running: an on-board
  * re-planning loop whose GPU memory is reserved once at start-up (an
  * allocation can synchronise the device or fail under fragmentation in
  * flight), or a process whose device memory belongs to another allocator.
- * Limit: count <= DPSO_NOALLOC_MAX_TOURS, else DPSO_ERR_RANGE before any
- * device work.  The first call on a device looks up the array's address with
- * that device current: make it before any stream capture.  All calls share the
- * array, so calls that overlap on the GPU (other streams, other host threads)
- * race; the caller must serialise them.
+ * Every call looks up the array's address on the current device (no
+ * allocation); the first call on a device loads the library's kernels there:
+ * make it before any stream capture.  All calls share the array, so calls
+ * that overlap on the GPU (other streams, other host threads) race; the
+ * caller must serialise them.
+ * Returns DPSO_OK; DPSO_ERR_ARG (null pointer, n < 3, count or max_moves < 0,
+ * an asymmetric cost matrix or a non-zero diagonal, a tour that is not a
+ * permutation); DPSO_ERR_RANGE (n > DPSO_MAX_N, a cost outside [0,
+ * DPSO_COST_MAX], or count > DPSO_NOALLOC_MAX_TOURS, the last before any
+ * device work); DPSO_ERR_CUDA; DPSO_ERR_INTERNAL.  It never returns
+ * DPSO_ERR_NO_MEMORY or DPSO_ERR_TIMEOUT.
  */
 #define DPSO_NOALLOC_MAX_TOURS 16350
 int dpso_two_opt_noalloc(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t count,

@@ -1,6 +1,8 @@
 // dpso_two_opt_noalloc: the standalone 2-opt entry point without any device
 // allocation.  Its scratch (error word, work queue, totals and per-tour pass /
-// move counts) lives in one fixed array inside the library.
+// move counts) lives in one fixed array inside the library.  It runs the
+// general (untiled) 2-opt kernel: the tiled kernel stages rows from four
+// row-shifted copies of the cost matrix, which would need an allocation.
 //
 // Who needs it: callers that must not allocate device memory while they run,
 // e.g. an on-board re-planning loop whose GPU memory is reserved once at
@@ -8,8 +10,6 @@
 // fragmentation mid-mission), or a host process whose device memory belongs to
 // another allocator (a framework's caching pool) that does not expect
 // allocations made behind its back.
-#include <mutex>
-
 #include "common.cuh"
 
 namespace dpso {
@@ -30,21 +30,14 @@ static_assert((kScratchBytes / 4 - kHeaderWords) / 2 == DPSO_NOALLOC_MAX_TOURS,
 // Every GPU that loads the library holds this array until the process exits.
 static __device__ __align__(256) unsigned int g_scratch[kScratchBytes / 4];
 
-// Device address of g_scratch per device, looked up once with that device
-// current (the host-side symbol is only a stand-in, not a device address).
-constexpr int kMaxDevices = 64;
-std::mutex g_mu;
-unsigned int* g_addr[kMaxDevices] = {};
-
-int scratch_address(int dev, unsigned int** out) {
-    if (dev < 0 || dev >= kMaxDevices) return DPSO_ERR_INTERNAL;
-    std::lock_guard<std::mutex> lock(g_mu);
-    if (!g_addr[dev]) {
-        void* p = nullptr;
-        if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess) return DPSO_ERR_CUDA;
-        g_addr[dev] = static_cast<unsigned int*>(p);
-    }
-    *out = g_addr[dev];
+// Device address of g_scratch on the current device (the host-side symbol is
+// only a stand-in, not a device address).  Looked up on every call, with the
+// caller's device current: the lookup allocates nothing, and an address kept
+// from an earlier call would be stale after the context were reset.
+int scratch_address(unsigned int** out) {
+    void* p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_scratch) != cudaSuccess || !p) return DPSO_ERR_CUDA;
+    *out = static_cast<unsigned int*>(p);
     return DPSO_OK;
 }
 
@@ -95,7 +88,7 @@ extern "C" int dpso_two_opt_noalloc(const int32_t* C_dev, int32_t n, uint16_t* t
         cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
         return DPSO_ERR_CUDA;
     unsigned int* scratch = nullptr;
-    int rc = scratch_address(dev, &scratch);
+    int rc = scratch_address(&scratch);
     if (rc) return rc;
     int* err = reinterpret_cast<int*>(scratch);
     const size_t used = sizeof(unsigned int) * (kHeaderWords + 2 * static_cast<size_t>(count));

@@ -37,6 +37,29 @@ def test_no_alloc_matches_allocating_entry_point_twice():
         assert got[3] > 0
 
 
+def test_no_alloc_call_leaves_device_memory_unchanged():
+    # the property the entry point exists for: after a first call (which may
+    # load the library's kernels on the device), a call takes no device
+    # memory, neither from the driver nor from torch's caching allocator
+    C_np, tours = inputs.random_cost_matrix(83, 8), inputs.random_tours(83, 33, 9)
+    n = C_np.shape[0]
+    C = torch.from_numpy(C_np).to(DEV)
+    T0 = torch.from_numpy(tours.view(np.int16).copy()).to(DEV)
+    T = T0.clone()
+    cost = torch.empty(len(tours), dtype=torch.int64, device=DEV)
+    dpso.dpso_two_opt_noalloc(C, n, T, len(tours), cost)
+    torch.cuda.synchronize()
+    free0, _ = torch.cuda.mem_get_info()
+    alloc0, reserved0 = torch.cuda.memory_allocated(), torch.cuda.memory_reserved()
+    for _ in range(3):
+        T.copy_(T0)                     # no allocation inside the measured stretch
+        dpso.dpso_two_opt_noalloc(C, n, T, len(tours), cost)
+    torch.cuda.synchronize()
+    free1, _ = torch.cuda.mem_get_info()
+    assert free1 == free0
+    assert (torch.cuda.memory_allocated(), torch.cuda.memory_reserved()) == (alloc0, reserved0)
+
+
 def test_no_alloc_rejects_counts_beyond_its_array():
     n = 10
     C = torch.from_numpy(inputs.random_cost_matrix(n, 1)).to(DEV)

@@ -90,6 +90,9 @@ namespace {
 // int32 sum cannot wrap; its delta (that minus the row's own edge, <= 2^29)
 // is at least 2^29 - 1 > 0, so padding never supplies an improving move.
 constexpr int kPadCost = (1 << 30) - 1;
+
+// Tours of at least this many viewpoints use segment tiles (see the kernel).
+constexpr int kSegmentMinN = 512;
 static_assert(2LL * DPSO_COST_MAX + kPadCost <= INT_MAX, "padding column overflows");
 static_assert(static_cast<long long>(kPadCost) - DPSO_COST_MAX > 0, "padding column improves");
 
@@ -143,9 +146,13 @@ constexpr int tiled_min_blocks() {
     return TG == 2 || (TPC == 1 && ROWS <= 16) ? 2 : (ROWS == 30 ? 4 : 3);
 }
 
-template <int ROWS, int TPC, int TG>
+// SEG: the launch holds tours long enough for segment tiles (n >=
+// kSegmentMinN; one tour per CTA).  Without it the segment-tile code is not
+// compiled into the kernel: short tours run measurably faster without it.
+template <int ROWS, int TPC, int TG, bool SEG>
 __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG>()))
     two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
+    static_assert(!SEG || TPC == 1, "segment tiles are instantiated for one tour per CTA");
     static_assert(TG == 1 || TPC == 1, "two tile subgroups need the whole CTA");
     constexpr int kRows = ROWS;        // positions per tile, one per lane
     constexpr int kStaged = ROWS + 1;  // cost rows staged per tile
@@ -167,6 +174,7 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
     // s_part: the tour's work item, then each pass's need-tile count, then
     // the winning column (each read after a barrier, before the next write)
     __shared__ int s_part[TPC], s_e0[TPC], s_e1[TPC], s_p[TPC];
+    __shared__ int s_mode[TPC * TG];         // short tours: 1 when the subgroup's tile is full
     __shared__ long long s_pf[TPC], s_f[TPC];
     // The tour's task descriptor, its running cost and the subgroups' counts of
     // evaluated pairs live in shared memory rather than registers: they are
@@ -235,6 +243,11 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
         const int nb32 = 2 * (rk64 + ((n + 1) & ~1));
         const int nl16 = 2 * (nb32 + (ntiles + 63) / 64 * 2);
         const int guard = 1000 + 100 * n;
+        // segment mode for tours whose rows are long enough that staging them
+        // costs more than the passes' fixed overhead (GB300 measurements:
+        // 10-25 % faster below n = 400 with partial tiles, 3 % slower at 600,
+        // 27 % slower at 1992)
+        const bool segmode = SEG && n >= kSegmentMinN;
 
         // The subgroup stages the `count` cost rows of the tile starting at I:
         // each warp posts kPerWarp rows, one bulk copy per lane (row r from
@@ -319,16 +332,21 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
             }
             const bool first = pb < 0;
             // The pass's tiles.  First pass: every grid tile, in full.  After a
-            // move (pa, pb): nseg segment tiles of rows pa.., starting at pa,
-            // whose staged rows pa..pb+1 also serve every row below pa over
-            // columns pa..pb (C is symmetric: C[x_i][x_j] = C[x_j][x_i]); then
-            // the grid tiles holding a row below pa whose cached improving
-            // move lay in a group touching pa..pb (its row is evaluated afresh
-            // in full).  Keys of the rows evaluated in full are reset first.
+            // move (pa, pb), long tours (segment mode): nseg segment tiles of
+            // rows pa.., starting at pa, whose staged rows pa..pb+1 also serve
+            // every row below pa over columns pa..pb (C is symmetric:
+            // C[x_i][x_j] = C[x_j][x_i]); then the grid tiles holding a row
+            // below pa whose cached improving move lay in a group touching
+            // pa..pb (its row is evaluated afresh in full).  Keys of the rows
+            // evaluated in full are reset first.  Short tours (rows of a few
+            // hundred bytes, cheap to stage): the grid tiles up to pb, last
+            // first; a tile holding rows of pa..pb, or a row whose cached move
+            // lay in a group touching pa..pb, in full, the others only in the
+            // groups of columns covering pa..pb.
             int nseg = 0;
-            if (first) {
+            if (segmode && first) {
                 for (int r = tid; r <= n - 3; r += GT) rowkey[r] = ~0ull;
-            } else {
+            } else if (segmode) {
                 nseg = (pb - pa + kRows) / kRows;
                 for (int r = tid; r <= min(pb, n - 3); r += GT) {
                     if (r >= pa) {
@@ -343,8 +361,8 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                     }
                 }
             }
-            group_sync<TPC>(grp);
-            if (!first && warp == 0) {
+            if (segmode) group_sync<TPC>(grp);  // (short tours: full tiles reset their own rows)
+            if (!first && segmode && warp == 0) {
                 // compact the need bitmask into a list (one warp; at most 32
                 // words: n <= 4168 tours have at most 521 grid tiles) and clear it
                 const int nw = (ntiles + 31) / 32;
@@ -361,9 +379,11 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                 if (lane < nw) needbits[lane] = 0u;
                 if (lane == 31) s_part[grp] = incl;  // (the work item is no longer needed this tour)
             }
-            group_sync<TPC>(grp);
-            const int ntot = first ? ntiles : nseg + s_part[grp];
-            // Tiles are taken in order (segment tiles first); with two
+            if (segmode && !first) group_sync<TPC>(grp);
+            const int tlast = first ? ntiles - 1 : min(ntiles - 1, pb / kRows);
+            const int ntot = first || !segmode ? tlast + 1 : nseg + s_part[grp];
+            // Tiles are taken in order (segment tiles first; short tours: the
+            // grid tiles from the last one down); with two
             // subgroups each takes the next one when it finishes its own
             // (s_tile, double-buffered by tile parity, published before the
             // subgroup barrier that the readers pass).
@@ -376,18 +396,39 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                 const int t = TG == 1 ? taken : s_tile[sg * 2 + par];
                 if (t >= ntot) break;
                 ++taken;
-                const bool seg = !first && t < nseg;
-                const int I = seg ? pa + t * kRows : (first ? t : needlist[t - nseg]) * kRows;
-                // staged rows I..I+count-1; rows evaluated in full I..rlast
+                const bool seg = segmode && !first && t < nseg;
+                const int I = !segmode || first ? (tlast - t) * kRows
+                                                : (seg ? pa + t * kRows : needlist[t - nseg] * kRows);
+                // staged rows I..I+count-1; rows evaluated I..rlast
                 const int count = seg ? min(kStaged, pb + 2 - I) : min(kStaged, n - 1 - I);
                 const int rlast = seg ? min(min(I + kRows - 1, pb), n - 3)
-                                      : (first ? n - 3 : min(pa - 1, n - 3));
+                                      : (first || !segmode ? n - 3 : min(pa - 1, n - 3));
                 stage(I, count);
                 if (wsg == 0) {
+                    if (!segmode) {
+                        // short tours: the tile's mode; a full tile starts its
+                        // rows' keys afresh.  Both before the barrier arrival
+                        // that the other warps acquire.
+                        bool full = first || (I <= pb && I + kRows - 1 >= pa);
+                        const int i = I + lane;
+                        const bool row_ok = lane < kRows && i <= n - 3;
+                        if (!full) {
+                            bool need = false;
+                            if (row_ok) {
+                                const unsigned long long k = rowkey[i];
+                                const int cmc = static_cast<int>(k & 0xffffu);
+                                need = k != ~0ull && cmc + 3 >= pa && cmc <= pb;
+                            }
+                            full = __any_sync(0xffffffffu, need);
+                        }
+                        if (full && row_ok) rowkey[i] = ~0ull;
+                        if (lane == 0) s_mode[sg] = full ? 1 : 0;
+                    }
                     __syncwarp();
                     if (lane == 0) mbar_expect(mbar, static_cast<unsigned>(count) * row_bytes);
                 }
                 stage_wait();
+                const bool full = segmode || s_mode[sg] != 0;
                 // the row this lane evaluates (lanes past the tile height idle
                 // on a valid row unless the tile splits the warp); byte offsets
                 // of its two staged rows (row start plus its 0..3 word shift)
@@ -406,16 +447,24 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                 // (a) the tile's rows over every column: groups of four from
                 // the even column at or below I+2 (records are read in pairs),
                 // contiguous per warp; the records past n are padding
-                const int cstart = (I + 2) & ~1;
-                const int ngroups = (n - cstart + 3) >> 2;
+                // (partial tiles of short tours: the groups of the tile's
+                // grid that hold pa..pb)
+                int cstart = (I + 2) & ~1, cstop = n;
+                if (!full) {
+                    cstart = I + 2 + ((max(pa, I + 2) - I - 2) & ~3);
+                    cstop = min(n, pb + 1);
+                }
+                const int ngroups = cstop > cstart ? (cstop - cstart + 3) >> 2 : 0;
                 const int g0 = (ngroups * wsg) / WSG, g1 = (ngroups * (wsg + 1)) / WSG;
                 if (wsg == 0) {
                     // pairs (i, j), i+2 <= j <= n-1, (i, j) != (0, n-1), of the rows
-                    // evaluated in full, and of the rows below pa against the
-                    // segment's columns (segment tiles)
-                    const bool row_ok = lane < kRows && I + lane <= rlast;
-                    int cnt = row_ok ? n - (I + lane) - 2 : 0;
-                    cnt -= (I + lane == 0 && cnt > 0) ? 1 : 0;
+                    // evaluated (in the columns cstart..E-1), and of the rows
+                    // below pa against the segment's columns (segment tiles)
+                    const int i = I + lane;
+                    const bool row_ok = lane < kRows && i <= rlast;
+                    const int E = min(cstart + 4 * ngroups, n);
+                    int cnt = row_ok ? max(0, E - max(cstart, i + 2)) : 0;
+                    cnt -= (i == 0 && E == n && cnt > 0) ? 1 : 0;
                     if (seg && pa > 0 && lane < kRows && I + lane <= pb) {
                         const int j = I + lane;
                         cnt += pa - (j == pa ? 1 : 0) - (j == n - 1 ? 1 : 0);
@@ -456,11 +505,14 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                         c += 4;
                         rp += 2;
                     };
-                    // groups starting below I+kStaged+1 hold the diagonal triangle
-                    const int cmask = min(cend, I + kStaged + 1);
+                    // groups starting below I+kStaged hold the diagonal triangle
+                    // (none on partial tiles)
+                    const int cmask = min(cend, I + kStaged);
                     while (c < cmask) group(true);
-                    // two groups at a time: sixteen gathers in flight
-                    while (c + 4 < cend) {
+                    // two groups at a time (sixteen gathers in flight) where the
+                    // register budget allows it: one long tour per 8-warp CTA
+                    constexpr bool kPairs = TPC == 1 && TG == 1 && ROWS <= 16;
+                    while (kPairs && c + 4 < cend) {
                         const int4 ra4 = rp[0], rb4 = rp[1], rc4 = rp[2], rd4 = rp[3];
                         const int v0 = at(r1, q) + at(r2, ra4.x) + ra4.y;
                         const int v1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w;
@@ -480,7 +532,7 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                         c += 8;
                         rp += 4;
                     }
-                    if (c < cend) group(false);
+                    while (c < cend) group(false);
                     // only improving moves enter the cache (m + the row's own
                     // edge term < 0; no overflow: m <= 2^31 - 1 - 2^29 on a valid column)
                     const int dl = m != INT_MAX ? m + smi2[rec2 + ie].y : 0;
@@ -681,32 +733,40 @@ size_t group_bytes(int n, int rows, int tg) {
     return (two_opt_tiled_smem(n, rows, tg) + 127) / 128 * 128;
 }
 
-template <int ROWS, int TPC, int TG>
+template <int ROWS, int TPC, int TG, bool SEG>
 cudaError_t launch_cfg(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     const size_t gb = group_bytes(b.max_n, ROWS, TG);
     const size_t smem = gb * TPC;
-    cudaError_t e = cudaFuncSetAttribute(two_opt_tiled_kernel<ROWS, TPC, TG>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
+    auto* kern = two_opt_tiled_kernel<ROWS, TPC, TG, SEG>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                          static_cast<int>(smem));
     if (e != cudaSuccess) return e;
     int per_sm = 0;
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two_opt_tiled_kernel<ROWS, TPC, TG>,
-                                                      kThreads * TG, smem);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads * TG, smem);
     if (e != cudaSuccess) return e;
     if (per_sm < 1) return cudaErrorInvalidConfiguration;
     const int grid = max(1, min((b.total + TPC - 1) / TPC, per_sm * num_sms));
-    two_opt_tiled_kernel<ROWS, TPC, TG>
-        <<<grid, kThreads * TG, smem, st>>>(b, static_cast<int>(gb / sizeof(int)));
+    kern<<<grid, kThreads * TG, smem, st>>>(b, static_cast<int>(gb / sizeof(int)));
     return cudaGetLastError();
 }
 
+// Launches with segment tiles when the launch holds a tour of at least
+// kSegmentMinN viewpoints and the shape has one tour per CTA (other shapes
+// use partial tiles for every tour).
 template <int ROWS>
 cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int tg, int num_sms, cudaStream_t st) {
-    if (tg == 2) return tpc == 1 ? launch_cfg<ROWS, 1, 2>(b, num_sms, st) : cudaErrorInvalidValue;
+    const bool seg = b.max_n >= kSegmentMinN;
+    if (tg == 2) {
+        if (tpc != 1) return cudaErrorInvalidValue;
+        return seg ? launch_cfg<ROWS, 1, 2, true>(b, num_sms, st)
+                   : launch_cfg<ROWS, 1, 2, false>(b, num_sms, st);
+    }
     switch (tpc) {
-        case 1: return launch_cfg<ROWS, 1, 1>(b, num_sms, st);
-        case 2: return launch_cfg<ROWS, 2, 1>(b, num_sms, st);
-        case 4: return launch_cfg<ROWS, 4, 1>(b, num_sms, st);
+        case 1:
+            return seg ? launch_cfg<ROWS, 1, 1, true>(b, num_sms, st)
+                       : launch_cfg<ROWS, 1, 1, false>(b, num_sms, st);
+        case 2: return launch_cfg<ROWS, 2, 1, false>(b, num_sms, st);
+        case 4: return launch_cfg<ROWS, 4, 1, false>(b, num_sms, st);
         default: return cudaErrorInvalidValue;
     }
 }

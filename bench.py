@@ -133,6 +133,33 @@ def oracle_sample(inst, swarm: int, warmup: int, generations: int, threads: int,
     return swarm * generations / dt, dt
 
 
+def _oracle_instance_worker(job):
+    """One spawned process: the oracle on one instance with `swarm`
+    particles for `generations` generations; returns (units, seconds)."""
+    inst, swarm, generations = job
+    import oracle
+    C, _ = oracle.cost_matrix(inst.xyz, inst.boxes)
+    sw = oracle.Swarm(C, inst.tags, swarm=swarm, seed=inst.seed)
+    t0 = time.perf_counter()
+    sw.run(generations)
+    return swarm * generations, time.perf_counter() - t0
+
+
+def oracle_pool_sample(insts, swarm: int, generations: int, procs: int):
+    """Times the oracle with one spawned process per host core over the
+    instances (each a `swarm`-particle swarm for `generations` generations);
+    returns (particle-iterations/s over the wall time, wall seconds).  The
+    pool is spawned, not forked, so it may start after CUDA is in use."""
+    import multiprocessing as mp
+    jobs = [(inst, min(swarm, inst.swarm), generations) for inst in insts]
+    ctx = mp.get_context("spawn")
+    t0 = time.perf_counter()
+    with ctx.Pool(procs) as pool:
+        got = pool.map(_oracle_instance_worker, jobs, chunksize=1)
+    wall = time.perf_counter() - t0
+    return sum(u for u, _ in got) / wall, wall
+
+
 def swarm_config(inst, exchange: str, world: int, steps: int) -> dict:
     """The `config` of a swarm workload's bench line (both arms)."""
     node_swap = exchange == "node-swap"
@@ -568,10 +595,12 @@ def batched_line(args):
 
     together, alone = swarms(), swarms()
     batch = dpso.Batch(together, stream)
-    rows, tpc, tg = batch.autotune(stream)
+    # the launch classes take their default shapes (from steady-state sweeps)
+    # unless --autotune asks dpso_batch_autotune to time the shapes that fit
+    rows, tpc, tg = batch.autotune(stream) if args.autotune else (0, 0, 0)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
 
-    def run(step_fn, steps):
+    def run(step_fn, steps, per_step=None):
         evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
                for _ in range(steps)]
         for k in range(steps):
@@ -580,7 +609,10 @@ def batched_line(args):
             step_fn()
             evs[k][1].record(stream)
         torch.cuda.synchronize()
-        return sum(a.elapsed_time(b) for a, b in evs)
+        ms = [a.elapsed_time(b) for a, b in evs]
+        if per_step is not None:
+            per_step.extend(ms)
+        return sum(ms)
 
     def solo_step():
         for sw in alone:
@@ -594,8 +626,12 @@ def batched_line(args):
     sampler = ClockSampler(gpu_index_for_smi(local))
     if dist:
         dist.barrier()
+    gen_ms = []
     with sampler:
-        ms_batch = max_over_ranks(run(lambda: batch.step(1, stream), args.steps), dist, "cuda")
+        sampler.start()
+        ms_batch = max_over_ranks(run(lambda: batch.step(1, stream), args.steps, gen_ms), dist,
+                                  "cuda")
+        sampler.stop()
         if dist:
             dist.barrier()
         ms_solo = max_over_ranks(run(solo_step, args.steps), dist, "cuda")
@@ -617,6 +653,19 @@ def batched_line(args):
     if rank != 0:
         return None
     ns = [i.n for i in all_insts]
+    import numpy as np
+    gm = np.array(gen_ms)
+    T = all_insts[0].iterations
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        procs = cpu_cores()
+        sample = all_insts[::8]
+        cval, csec = oracle_pool_sample(sample, 2, 1, procs)
+        cpu = {"value": cval, "unit": UNIT, "cores": procs, "kind": "oracle",
+               "sample": f"{len(sample)} of the {len(all_insts)} instances (every 8th), each an "
+                         f"oracle swarm of 2 particles for its first generation, one spawned "
+                         f"process per host core ({csec:.1f} s wall)",
+               "cpu": cpu_model()}
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_batch / args.steps, "higher_is_better": True,
@@ -627,10 +676,23 @@ def batched_line(args):
                    "l2": "flushed between timed generations (256 MiB write)"},
         "batched": {"one_per_launch_value": solo_value, "speedup": value / solo_value,
                     "one_per_launch_ms_per_step": ms_solo / args.steps,
-                    "identical_states": identical, "two_opt_rows": rows, "two_opt_tours_per_cta": tpc,
-                    "two_opt_tiles_in_flight": tg,
-                    "two_opt_pairs_per_s_over_step": pairs / (ms_batch / 1e3)},
-        "gpu_launches": None, "roofline": None, "cpu_baseline": None, "e2e": None,
+                    "identical_states": identical,
+                    "two_opt_shapes": (f"autotuned; last class ({rows}, {tpc}, {tg})" if args.autotune
+                                       else "each class's default shape"),
+                    "two_opt_pairs_per_s_over_step": pairs / (ms_batch / 1e3),
+                    # every member advances one generation per replay of the
+                    # batch graph: a generation's latency is the latency of
+                    # each member's step, and a member's solve of T
+                    # generations finishes with the batch
+                    "generation_latency_ms": {"p50": float(np.percentile(gm, 50)),
+                                              "p99": float(np.percentile(gm, 99)),
+                                              "max": float(gm.max())},
+                    "instance_solve_latency_s": {
+                        "generations": T,
+                        "p50": float(np.percentile(gm, 50)) * T / 1e3,
+                        "p99": float(np.percentile(gm, 99)) * T / 1e3,
+                        "what": "T generations at the measured per-generation p50 / p99"}},
+        "gpu_launches": None, "roofline": None, "cpu_baseline": cpu, "e2e": None,
         "clocks": sampler.summary(),
     }
 
@@ -655,7 +717,8 @@ def serving_line(args):
     dpso.dpso_plan(w.xyz, w.boxes, w.tags, cp, params[0], w.seed, 1)
 
     policy = dpso.SERVE_SHORTEST_FIRST if args.policy == "shortest" else dpso.SERVE_ARRIVAL_ORDER
-    server = dpso.Server(dpso.default_server_params(max_active=args.max_active, policy=policy))
+    server = dpso.Server(dpso.default_server_params(max_active=args.max_active, policy=policy,
+                                                    lanes=args.lanes))
     sampler = ClockSampler(gpu_index_for_smi(0))
     ids = []
     with sampler:
@@ -704,7 +767,8 @@ def serving_line(args):
                     "one_per_launch_requests_per_s": len(stream_reqs) / solo_s,
                     "speedup": solo_s / served_s, "identical_tours": identical,
                     "peak_active": sstats["peak_active"], "ticks": sstats["ticks"],
-                    "policy": args.policy, "max_active": args.max_active},
+                    "policy": args.policy, "max_active": args.max_active,
+                    "lanes": args.lanes},
         "gpu_launches": None, "roofline": None, "cpu_baseline": None,
         "e2e": {"value": units / served_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(np.mean([i.xyz.nbytes + i.boxes.nbytes + i.tags.nbytes
@@ -847,11 +911,15 @@ def main(argv=None):
     ap.add_argument("--tours", type=int, default=152, help="two-opt: random tours per call")
     ap.add_argument("--max-moves", type=int, default=30, help="two-opt: move cap per tour")
     ap.add_argument("--instances", type=int, default=256, help="batched: instances")
+    ap.add_argument("--autotune", action="store_true",
+                    help="batched: dpso_batch_autotune the launch classes' shapes")
     ap.add_argument("--requests", type=int, default=48, help="serving: requests")
     ap.add_argument("--max-n", type=int, default=400, help="serving: largest request taken")
-    ap.add_argument("--policy", default="shortest", choices=["arrival", "shortest"],
+    ap.add_argument("--policy", default="arrival", choices=["arrival", "shortest"],
                     help="serving: admission order")
     ap.add_argument("--max-active", type=int, default=16, help="serving: running requests at most")
+    ap.add_argument("--lanes", type=int, default=4,
+                    help="serving: size-class lanes (1: one lock-step batch)")
     ap.add_argument("--exchange", default="2-opt", choices=["2-opt", "node-swap"],
                     help="edge exchange of the swarm workloads")
     ap.add_argument("--swarm", type=int, default=0,

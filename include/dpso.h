@@ -389,19 +389,26 @@ int dpso_plan(const double *xyz_host, int32_t n, const double *boxes_host, int32
  * Re-planning server (the on-line re-planning requirement of Sec. 1 served
  * for many requests at once; the paper has no server of its own).
  *
- * One engine thread per server, with its own CUDA stream on the device that
- * is current at creation.  Requests are copied at submission and queued;
- * each engine tick admits queued requests (in the order `policy` sets) while
- * fewer than
- * `max_active` are running and their estimated device footprint fits in
- * `memory_budget_bytes` (cost matrix by dpso_cost_matrix, swarm by
- * dpso_init; the state then stays on the device until the request ends),
- * groups every running request into one batch (dpso_batch_*) and advances it
- * by the smallest remaining generation budget, at most
- * `generations_per_tick` generations.  No request runs past its own budget,
- * so each result (tour and cost) is bit-identical to dpso_plan of the same
- * request alone, whatever else is in the mix.  Finished requests leave the
- * batch at the next tick and release their memory.
+ * Requests are served in `lanes` size classes by viewpoint count n: lane 0
+ * takes n < 100, lane k (k >= 1) 100 * 2^(k-1) <= n < 100 * 2^k, the last
+ * lane every larger n.  Each lane has an engine thread and a CUDA stream of
+ * its own on the device that is current at creation, so the lanes' launches
+ * overlap on the device and a small request's generations do not wait for a
+ * large one's.  Requests are copied at submission and queued; each tick of
+ * a lane admits queued requests of its class (in the order `policy` sets)
+ * while fewer than `max_active` requests are running in the whole server
+ * (a lane holding max_active / lanes of them admits more only while no
+ * other lane has requests waiting; lanes of smaller requests run on streams
+ * of higher priority) and their estimated device footprint fits in
+ * `memory_budget_bytes` (cost
+ * matrix by dpso_cost_matrix, swarm by dpso_init; the state then stays on
+ * the device until the request ends), groups the lane's running requests
+ * into one batch (dpso_batch_*) and advances it by their smallest remaining
+ * generation budget, at most `generations_per_tick` generations.  No request
+ * runs past its own budget, so each result (tour and cost) is bit-identical
+ * to dpso_plan of the same request alone, whatever else is in the mix.
+ * Finished requests leave the batch at the lane's next tick and release
+ * their memory.
  */
 typedef struct dpso_server dpso_server;
 
@@ -413,12 +420,15 @@ typedef struct dpso_server dpso_server;
 #define DPSO_SERVE_ARRIVAL_ORDER 0
 #define DPSO_SERVE_SHORTEST_FIRST 1
 
+#define DPSO_SERVE_MAX_LANES 8
+
 typedef struct {
     uint64_t memory_budget_bytes; /* 0: half of the free device memory at creation */
-    int32_t max_active;           /* running requests at most (default 64) */
+    int32_t max_active;           /* running requests at most, all lanes (default 64) */
     int32_t generations_per_tick; /* generations per engine tick at most (default 8) */
     int32_t policy;               /* DPSO_SERVE_* (default arrival order) */
-    int32_t reserved;             /* must be 0 */
+    int32_t lanes;                /* size-class lanes, 1..DPSO_SERVE_MAX_LANES; 0: 4
+                                     (the default) */
 } dpso_server_params;
 
 typedef struct {
@@ -444,7 +454,9 @@ typedef struct {
 } dpso_server_stats;
 
 void dpso_default_server_params(dpso_server_params *p);
-/* Starts the engine.  Errors: DPSO_ERR_ARG, DPSO_ERR_CUDA. */
+/* Starts the engines (one per lane).  Errors: DPSO_ERR_ARG (max_active or
+ * generations_per_tick < 1, an unknown policy, lanes outside 0..8),
+ * DPSO_ERR_CUDA. */
 int dpso_server_create(dpso_server **out, const dpso_server_params *p);
 /* Queues a request (host buffers copied; the caller may free them at once)
  * and returns its id (> 0).  Does not block on the device.  Errors:

@@ -579,7 +579,7 @@ cudaError_t run_warp_pass(const WarpArgs& W, cudaStream_t st) {
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     const int smem = kWarpsPerBlock * (kWarpOpen + kWarpSlots) * static_cast<int>(sizeof(unsigned long long));
     if (e == cudaSuccess)
-        e = cudaFuncSetAttribute(astar_warp_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+        e = raise_smem_limit(astar_warp_kernel, smem);
     if (e != cudaSuccess) return e;
     const int blocks = std::max(1, std::min(sms, (W.npairs + kWarpsPerBlock - 1) / kWarpsPerBlock));
     astar_warp_kernel<<<blocks, 32 * kWarpsPerBlock, smem, st>>>(W);

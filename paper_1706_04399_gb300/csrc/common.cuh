@@ -221,6 +221,25 @@ cudaError_t launch_two_opt(const TwoOptBatch& b, int num_sms, cudaStream_t st);
 // ---- two_opt_tiled.cu: pipelined tiled variant (needs the shifted copies) ----
 // Row pitch (words) of the shifted copies and of the staged rows: room for a
 // shift of up to 3 words, a multiple of 4 words (16-byte rows), ldq/4 odd.
+// Raises a kernel's dynamic shared-memory limit to the most the device
+// allows beside the kernel's static shared memory, and checks that `smem`
+// bytes fit.  Every caller sets the same value, so launches of one kernel
+// with different sizes from several host threads never lower the limit
+// under one another (the attribute is per kernel, not per launch).
+template <typename Kernel>
+inline cudaError_t raise_smem_limit(Kernel* kernel, size_t smem) {
+    int dev = 0, optin = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess)
+        e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+    cudaFuncAttributes fa{};
+    if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, kernel);
+    if (e != cudaSuccess) return e;
+    const int dyn_max = optin - static_cast<int>(fa.sharedSizeBytes);
+    if (dyn_max < 0 || smem > static_cast<size_t>(dyn_max)) return cudaErrorInvalidValue;
+    return cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, dyn_max);
+}
+
 __host__ __device__ inline int shifted_ld(int n) {
     int q = (n + 3 + 3) / 4 * 4;
     if (((q / 4) & 1) == 0) q += 4;

@@ -294,9 +294,7 @@ __global__ void __launch_bounds__(kThreads, 3) node_swap_tiled_kernel(TwoOptBatc
 template <int ROWS>
 cudaError_t launch_ns(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     const size_t smem = node_swap_tiled_smem(b.max_n, ROWS);
-    cudaError_t e = cudaFuncSetAttribute(node_swap_tiled_kernel<ROWS>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(node_swap_tiled_kernel<ROWS>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, node_swap_tiled_kernel<ROWS>,

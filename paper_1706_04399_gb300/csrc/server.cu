@@ -1,16 +1,21 @@
 // Re-planning server: continuous batching of DPSO solves (the "online
 // re-planning" requirement of Sec. 1 served many requests at a time).
 //
-// An engine thread owns one CUDA stream.  Each tick it
-//   1. admits queued requests in arrival order while slots and the device
-//      memory budget allow (cost matrix, swarm initialisation);
-//   2. rebuilds the batch when the set of active requests changed;
-//   3. advances every active request by the smallest remaining generation
-//      budget (capped per tick), so no request runs past its own budget and
-//      each result equals a solo dpso_plan of the same request;
+// Requests are served in size-class lanes (by viewpoint count: below 100,
+// 100-199, 200-399, ..., the last lane taking the rest).  Each lane has an
+// engine thread and a CUDA stream of its own, so the lanes' launches overlap
+// on the device and a small request's generations do not wait for a large
+// one's.  Each tick a lane
+//   1. admits queued requests of its class (in arrival order, or least
+//      estimated work first) while the server's slots and device memory
+//      budget allow (cost matrix, swarm initialisation);
+//   2. rebuilds its batch when its set of active requests changed;
+//   3. advances every active request of the lane by the smallest remaining
+//      generation budget (capped per tick), so no request runs past its own
+//      budget and each result equals a solo dpso_plan of the same request;
 //   4. retires finished requests (best tour copied out, memory released).
-// Requests arriving while others run join at the next tick and their
-// generations share the same launches.
+// Requests arriving while others run join their lane at its next tick and
+// their generations share the lane's launches.
 #include <math.h>
 #include <string.h>
 
@@ -33,6 +38,7 @@ using Clock = std::chrono::steady_clock;
 
 struct Request {
     int64_t id = 0;
+    int lane = 0;
     std::vector<double> xyz, boxes;
     std::vector<int32_t> tags;
     bool has_tags = false;
@@ -80,22 +86,36 @@ size_t request_footprint(int n, int m, int S, int T, int flags) {
 
 }  // namespace
 
+// One size-class lane: engine thread, stream, running requests and batch
+// (the last three touched only by the lane's thread).
+struct Lane {
+    int index = 0;
+    int admitted = 0;  // requests of this lane admitted and not yet retired (under mu)
+    cudaStream_t stream = nullptr;
+    std::thread engine;
+    std::vector<Active> active;
+    dpso_batch* batch = nullptr;
+    bool dirty = false;
+};
+
 struct dpso_server {
     dpso_server_params prm{};
     int device = 0;
-    cudaStream_t stream = nullptr;
     std::mutex mu;
     std::condition_variable cv;
     std::deque<std::shared_ptr<Request>> queue;
     std::map<int64_t, std::shared_ptr<Request>> all;
     int64_t next_id = 1;
     bool stop = false;
-    std::thread engine;
-    // engine-side state
-    std::vector<Active> active;
-    dpso_batch* batch = nullptr;
-    bool dirty = false;
+    std::vector<std::unique_ptr<Lane>> lanes;
+    // The lanes' library calls (admission, batch building, enqueueing,
+    // retirement) take turns under lib_mu, so that no lane frees device
+    // memory or captures a graph while another captures; only the waits for
+    // their streams run concurrently (and the launches on the device).
+    std::mutex lib_mu;
+    // shared by the lanes, under mu
     size_t used = 0;
+    int n_active = 0;  // requests admitted and not yet retired, all lanes
     // statistics
     dpso_server_stats st{};
     Clock::time_point start;
@@ -103,9 +123,16 @@ struct dpso_server {
 
 namespace {
 
-// Cost matrix and swarm for one request on the engine stream.
-int admit(dpso_server* sv, Request& r, dpso_swarm** out) {
-    cudaStream_t st = sv->stream;
+// The lane of a request of n viewpoints: 0 below 100, then one lane per
+// doubling (100-199, 200-399, ...), the last lane taking the rest.
+int lane_of(int n, int lanes) {
+    int k = 0;
+    while (k + 1 < lanes && n >= (100 << k)) ++k;
+    return k;
+}
+
+// Cost matrix and swarm for one request on its lane's stream.
+int admit(cudaStream_t st, Request& r, dpso_swarm** out) {
     double *xyz = nullptr, *boxes = nullptr;
     int32_t* C = nullptr;
     int rc = DPSO_OK;
@@ -131,9 +158,13 @@ int admit(dpso_server* sv, Request& r, dpso_swarm** out) {
 
 // Publishes a request's outcome and releases its share of the budget (the
 // caller has already freed its device memory).
-void finish(dpso_server* sv, Request& r, int status, bool release) {
+void finish(dpso_server* sv, Lane* ln, Request& r, int status, bool release) {
     std::lock_guard<std::mutex> lock(sv->mu);
-    if (release) sv->used -= r.footprint;
+    if (release) {
+        sv->used -= r.footprint;
+        sv->n_active -= 1;
+        ln->admitted -= 1;
+    }
     r.status = status;
     r.latency_s = std::chrono::duration<double>(Clock::now() - r.submitted).count();
     if (status == 1) {
@@ -145,14 +176,17 @@ void finish(dpso_server* sv, Request& r, int status, bool release) {
     sv->cv.notify_all();
 }
 
-void engine_loop(dpso_server* sv) {
+void engine_loop(dpso_server* sv, Lane* ln) {
     cudaSetDevice(sv->device);
     for (;;) {
         // 1. admission
         {
             std::unique_lock<std::mutex> lock(sv->mu);
-            if (sv->active.empty() && sv->queue.empty() && !sv->stop)
-                sv->cv.wait_for(lock, std::chrono::milliseconds(20));
+            if (ln->active.empty() && !sv->stop) {
+                bool mine = false;
+                for (const auto& q : sv->queue) mine = mine || q->lane == ln->index;
+                if (!mine) sv->cv.wait_for(lock, std::chrono::milliseconds(20));
+            }
             if (sv->stop) break;
         }
         for (;;) {
@@ -160,85 +194,111 @@ void engine_loop(dpso_server* sv) {
             bool never_fits = false;
             {
                 std::lock_guard<std::mutex> lock(sv->mu);
-                if (sv->queue.empty() ||
-                    static_cast<int>(sv->active.size()) >= sv->prm.max_active)
-                    break;
-                // the next request: the oldest, or the one with the least
-                // estimated work (earliest submitted among equals)
-                auto pick = sv->queue.begin();
-                if (sv->prm.policy == DPSO_SERVE_SHORTEST_FIRST)
-                    for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it)
-                        if ((*it)->work < (*pick)->work) pick = it;
+                if (sv->n_active >= sv->prm.max_active) break;
+                // a lane holds at most its share of the slots while another
+                // lane has requests waiting
+                const int share = std::max(1, sv->prm.max_active / sv->prm.lanes);
+                if (ln->admitted >= share) {
+                    bool others = false;
+                    for (const auto& q : sv->queue) others = others || q->lane != ln->index;
+                    if (others) break;
+                }
+                // the lane's next request: the oldest, or the one with the
+                // least estimated work (earliest submitted among equals)
+                auto pick = sv->queue.end();
+                for (auto it = sv->queue.begin(); it != sv->queue.end(); ++it) {
+                    if ((*it)->lane != ln->index) continue;
+                    if (pick == sv->queue.end()) {
+                        pick = it;
+                        if (sv->prm.policy != DPSO_SERVE_SHORTEST_FIRST) break;
+                    } else if ((*it)->work < (*pick)->work) {
+                        pick = it;
+                    }
+                }
+                if (pick == sv->queue.end()) break;
                 r = *pick;
                 never_fits = r->footprint > sv->prm.memory_budget_bytes;
                 if (!never_fits && sv->used + r->footprint > sv->prm.memory_budget_bytes) break;
                 sv->queue.erase(pick);
-                if (!never_fits) sv->used += r->footprint;
+                if (!never_fits) {
+                    sv->used += r->footprint;
+                    sv->n_active += 1;
+                    ln->admitted += 1;
+                }
             }
             if (never_fits) {
-                finish(sv, *r, DPSO_ERR_NO_MEMORY, false);
+                finish(sv, ln, *r, DPSO_ERR_NO_MEMORY, false);
                 continue;
             }
             dpso_swarm* sw = nullptr;
-            const int rc = admit(sv, *r, &sw);
+            int rc;
+            {
+                std::lock_guard<std::mutex> lib(sv->lib_mu);
+                rc = admit(ln->stream, *r, &sw);
+            }
             if (rc) {
-                finish(sv, *r, rc, true);
+                finish(sv, ln, *r, rc, true);
                 continue;
             }
-            sv->active.push_back(Active{r, sw, r->iterations, 0});
-            if (r->iterations > 0) sv->dirty = true;
+            ln->active.push_back(Active{r, sw, r->iterations, 0});
+            if (r->iterations > 0) ln->dirty = true;
         }
         std::vector<Active> running;
-        for (const Active& a : sv->active)
+        for (const Active& a : ln->active)
             if (a.remaining > 0) running.push_back(a);
-        // 2-3. advance every running request together
+        // 2-3. advance every running request of the lane together
         if (!running.empty()) {
-            if (sv->dirty || !sv->batch) {
-                if (sv->batch) dpso_batch_destroy(sv->batch);
-                sv->batch = nullptr;
+            std::unique_lock<std::mutex> lib(sv->lib_mu);
+            if (ln->dirty || !ln->batch) {
+                if (ln->batch) dpso_batch_destroy(ln->batch);
+                ln->batch = nullptr;
                 std::vector<dpso_swarm*> members;
                 for (const Active& a : running) members.push_back(a.swarm);
-                int rc = dpso_batch_create(&sv->batch, members.data(),
-                                           static_cast<int32_t>(members.size()), sv->stream);
+                int rc = dpso_batch_create(&ln->batch, members.data(),
+                                           static_cast<int32_t>(members.size()), ln->stream);
                 if (rc) {  // the running requests fail with the batch
-                    for (Active& a : sv->active)
+                    for (Active& a : ln->active)
                         if (a.remaining > 0) {
                             a.fail = rc;
                             a.remaining = -1;
                         }
                 }
-                sv->dirty = false;
+                ln->dirty = false;
             }
-            if (sv->batch) {
+            if (ln->batch) {
                 int g = sv->prm.generations_per_tick;
                 for (const Active& a : running) g = std::min(g, a.remaining);
-                const int rc = dpso_batch_step(sv->batch, g, sv->stream);
-                if (rc == DPSO_OK && cudaStreamSynchronize(sv->stream) == cudaSuccess) {
-                    for (Active& a : sv->active)
+                const int rc = dpso_batch_step(ln->batch, g, ln->stream);
+                lib.unlock();
+                if (rc == DPSO_OK && cudaStreamSynchronize(ln->stream) == cudaSuccess) {
+                    for (Active& a : ln->active)
                         if (a.remaining > 0) a.remaining -= g;
                     std::lock_guard<std::mutex> lock(sv->mu);
                     sv->st.ticks += 1;
-                    sv->st.peak_active =
-                        std::max<int32_t>(sv->st.peak_active, static_cast<int32_t>(running.size()));
+                    sv->st.peak_active = std::max<int32_t>(sv->st.peak_active, sv->n_active);
                 } else {
-                    for (Active& a : sv->active)
+                    for (Active& a : ln->active)
                         if (a.remaining > 0) {
                             a.fail = rc ? rc : DPSO_ERR_CUDA;
                             a.remaining = -1;
                         }
                 }
             }
+        } else if (!ln->active.empty()) {
+            std::lock_guard<std::mutex> lock(sv->mu);
+            sv->st.peak_active = std::max<int32_t>(sv->st.peak_active, sv->n_active);
         }
         // 4. retirement: the batch goes first (it refers to its members)
         bool any_done = false;
-        for (const Active& a : sv->active) any_done = any_done || a.remaining <= 0;
+        for (const Active& a : ln->active) any_done = any_done || a.remaining <= 0;
         if (any_done) {
-            if (sv->batch) {
-                dpso_batch_destroy(sv->batch);
-                sv->batch = nullptr;
+            std::lock_guard<std::mutex> lib(sv->lib_mu);
+            if (ln->batch) {
+                dpso_batch_destroy(ln->batch);
+                ln->batch = nullptr;
             }
             std::vector<Active> keep;
-            for (Active& a : sv->active) {
+            for (Active& a : ln->active) {
                 if (a.remaining > 0) {
                     keep.push_back(a);
                     continue;
@@ -253,15 +313,17 @@ void engine_loop(dpso_server* sv) {
                     status = rc ? rc : 1;
                 }
                 dpso_destroy(a.swarm);
-                finish(sv, r, status, true);
+                finish(sv, ln, r, status, true);
             }
-            sv->active.swap(keep);
-            sv->dirty = true;
+            ln->active.swap(keep);
+            ln->dirty = true;
         }
     }
-    if (sv->batch) dpso_batch_destroy(sv->batch);
-    for (Active& a : sv->active) dpso_destroy(a.swarm);
-    sv->active.clear();
+    std::lock_guard<std::mutex> lib(sv->lib_mu);
+    if (ln->batch) dpso_batch_destroy(ln->batch);
+    ln->batch = nullptr;
+    for (Active& a : ln->active) dpso_destroy(a.swarm);
+    ln->active.clear();
 }
 
 }  // namespace
@@ -274,33 +336,45 @@ void dpso_default_server_params(dpso_server_params* p) {
     p->max_active = 64;
     p->generations_per_tick = 8;
     p->policy = DPSO_SERVE_ARRIVAL_ORDER;
-    p->reserved = 0;
+    p->lanes = 4;
 }
 
 int dpso_server_create(dpso_server** out, const dpso_server_params* p) {
     if (!out || !p || p->max_active < 1 || p->generations_per_tick < 1 ||
         (p->policy != DPSO_SERVE_ARRIVAL_ORDER && p->policy != DPSO_SERVE_SHORTEST_FIRST) ||
-        p->reserved != 0)
+        p->lanes < 0 || p->lanes > DPSO_SERVE_MAX_LANES)
         return DPSO_ERR_ARG;
     *out = nullptr;
     dpso_server* sv = new dpso_server();
     sv->prm = *p;
-    if (cudaGetDevice(&sv->device) != cudaSuccess ||
-        cudaStreamCreateWithFlags(&sv->stream, cudaStreamNonBlocking) != cudaSuccess) {
+    if (sv->prm.lanes == 0) sv->prm.lanes = 4;
+    auto fail = [&](int code) {
+        for (auto& ln : sv->lanes)
+            if (ln->stream) cudaStreamDestroy(ln->stream);
         delete sv;
-        return DPSO_ERR_CUDA;
+        return code;
+    };
+    if (cudaGetDevice(&sv->device) != cudaSuccess) return fail(DPSO_ERR_CUDA);
+    // lanes of smaller requests get higher stream priorities: when a large
+    // lane's generation frees the SMs, a small lane's waiting kernels go first
+    int least = 0, greatest = 0;
+    if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess)
+        return fail(DPSO_ERR_CUDA);
+    for (int k = 0; k < sv->prm.lanes; ++k) {
+        auto ln = std::make_unique<Lane>();
+        ln->index = k;
+        const int prio = std::min(least, greatest + k);  // greatest is numerically lowest
+        if (cudaStreamCreateWithPriority(&ln->stream, cudaStreamNonBlocking, prio) != cudaSuccess)
+            return fail(DPSO_ERR_CUDA);
+        sv->lanes.push_back(std::move(ln));
     }
     if (sv->prm.memory_budget_bytes == 0) {
         size_t free_b = 0, total_b = 0;
-        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) {
-            cudaStreamDestroy(sv->stream);
-            delete sv;
-            return DPSO_ERR_CUDA;
-        }
+        if (cudaMemGetInfo(&free_b, &total_b) != cudaSuccess) return fail(DPSO_ERR_CUDA);
         sv->prm.memory_budget_bytes = free_b / 2;
     }
     sv->start = Clock::now();
-    sv->engine = std::thread(engine_loop, sv);
+    for (auto& ln : sv->lanes) ln->engine = std::thread(engine_loop, sv, ln.get());
     *out = sv;
     return DPSO_OK;
 }
@@ -339,6 +413,7 @@ int dpso_server_submit(dpso_server* sv, const dpso_request* r, int64_t* id) {
     q->footprint = request_footprint(r->n, r->m, r->params.swarm, r->iterations, r->params.flags);
     q->work = static_cast<double>(r->params.swarm) * r->iterations * r->n * r->n * r->n;
     q->submitted = Clock::now();
+    q->lane = lane_of(q->n, sv->prm.lanes);
     std::lock_guard<std::mutex> lock(sv->mu);
     q->id = sv->next_id++;
     sv->all[q->id] = q;
@@ -399,9 +474,11 @@ void dpso_server_destroy(dpso_server* sv) {
         sv->stop = true;
         sv->cv.notify_all();
     }
-    if (sv->engine.joinable()) sv->engine.join();
-    cudaStreamSynchronize(sv->stream);
-    cudaStreamDestroy(sv->stream);
+    for (auto& ln : sv->lanes) {
+        if (ln->engine.joinable()) ln->engine.join();
+        cudaStreamSynchronize(ln->stream);
+        cudaStreamDestroy(ln->stream);
+    }
     delete sv;
 }
 

@@ -594,9 +594,7 @@ cudaError_t launch_move(const BatchView& b, cudaStream_t st) {
     if (b.total <= 0) return cudaSuccess;
     const int w = move_warps(b);
     const size_t smem = static_cast<size_t>(b.arrays) * b.max_ldn * sizeof(uint16_t) * w;
-    const cudaError_t e = cudaFuncSetAttribute(move_kernel,
-                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                               static_cast<int>(smem));
+    const cudaError_t e = raise_smem_limit(move_kernel, smem);
     if (e != cudaSuccess) return e;
     move_kernel<<<(b.total + w - 1) / w, 32 * w, smem, st>>>(b);
     return cudaGetLastError();

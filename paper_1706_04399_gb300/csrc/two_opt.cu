@@ -209,9 +209,7 @@ __global__ void __launch_bounds__(kWarps * 32) two_opt_kernel(TwoOptBatch b) {
 template <int R>
 cudaError_t launch_r(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     const size_t smem = two_opt_smem(b.max_n, R);
-    cudaError_t e = cudaFuncSetAttribute(two_opt_kernel<R>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(two_opt_kernel<R>, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, two_opt_kernel<R>, kWarps * 32, smem);

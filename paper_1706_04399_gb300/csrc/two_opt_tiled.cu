@@ -146,9 +146,9 @@ constexpr int tiled_min_blocks() {
     return TG == 2 || (TPC == 1 && ROWS <= 16) ? 2 : (ROWS == 30 ? 4 : 3);
 }
 
-// SEG: the launch holds tours long enough for segment tiles (n >=
-// kSegmentMinN; one tour per CTA).  Without it the segment-tile code is not
-// compiled into the kernel: short tours run measurably faster without it.
+// SEG: segment tiles (launches whose longest tour has n >= kSegmentMinN;
+// one tour per CTA), else partial tiles.  Each kernel holds only its own
+// mode's code: with both compiled in, short tours ran 6-10 % slower.
 template <int ROWS, int TPC, int TG, bool SEG>
 __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG>()))
     two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
@@ -243,11 +243,12 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
         const int nb32 = 2 * (rk64 + ((n + 1) & ~1));
         const int nl16 = 2 * (nb32 + (ntiles + 63) / 64 * 2);
         const int guard = 1000 + 100 * n;
-        // segment mode for tours whose rows are long enough that staging them
-        // costs more than the passes' fixed overhead (GB300 measurements:
-        // 10-25 % faster below n = 400 with partial tiles, 3 % slower at 600,
-        // 27 % slower at 1992)
-        const bool segmode = SEG && n >= kSegmentMinN;
+        // segment tiles in launches holding long tours, whose rows are long
+        // enough that staging them costs more than the passes' fixed overhead
+        // (GB300 measurements: partial tiles 10-25 % faster below n = 400,
+        // 3 % slower at 600, 27 % slower at 1992); every tour of such a
+        // launch takes them, so the partial-tile path is not compiled in
+        constexpr bool segmode = SEG;
 
         // The subgroup stages the `count` cost rows of the tile starting at I:
         // each warp posts kPerWarp rows, one bulk copy per lane (row r from
@@ -738,8 +739,7 @@ cudaError_t launch_cfg(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     const size_t gb = group_bytes(b.max_n, ROWS, TG);
     const size_t smem = gb * TPC;
     auto* kern = two_opt_tiled_kernel<ROWS, TPC, TG, SEG>;
-    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         static_cast<int>(smem));
+    cudaError_t e = raise_smem_limit(kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
     e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads * TG, smem);
@@ -750,9 +750,10 @@ cudaError_t launch_cfg(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-// Launches with segment tiles when the launch holds a tour of at least
-// kSegmentMinN viewpoints and the shape has one tour per CTA (other shapes
-// use partial tiles for every tour).
+// Launches with segment tiles (for every tour) when the launch holds a tour
+// of at least kSegmentMinN viewpoints and the shape has one tour per CTA;
+// other shapes use partial tiles for every tour.  Results are the same
+// either way.
 template <int ROWS>
 cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int tg, int num_sms, cudaStream_t st) {
     const bool seg = b.max_n >= kSegmentMinN;

@@ -89,7 +89,7 @@ class dpso_astar_params(ctypes.Structure):
 class dpso_server_params(ctypes.Structure):
     _fields_ = [("memory_budget_bytes", ctypes.c_uint64), ("max_active", ctypes.c_int32),
                 ("generations_per_tick", ctypes.c_int32), ("policy", ctypes.c_int32),
-                ("reserved", ctypes.c_int32)]
+                ("lanes", ctypes.c_int32)]
 
 
 class dpso_request(ctypes.Structure):

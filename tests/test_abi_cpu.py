@@ -69,12 +69,13 @@ def test_server_host_side_checks(libpath):
     from paper_1706_04399_gb300 import dpso, inputs
     L = dpso.lib()
     sp = dpso.default_server_params()
-    assert (sp.memory_budget_bytes, sp.max_active, sp.generations_per_tick, sp.policy) == \
-        (0, 64, 8, dpso.SERVE_ARRIVAL_ORDER)
+    assert (sp.memory_budget_bytes, sp.max_active, sp.generations_per_tick, sp.policy,
+            sp.lanes) == (0, 64, 8, dpso.SERVE_ARRIVAL_ORDER, 4)
     h = ctypes.c_void_p()
     for bad in (dpso.default_server_params(max_active=0),
                 dpso.default_server_params(generations_per_tick=0),
-                dpso.default_server_params(policy=2), dpso.default_server_params(reserved=1)):
+                dpso.default_server_params(policy=2), dpso.default_server_params(lanes=9),
+                dpso.default_server_params(lanes=-1)):
         assert L.dpso_server_create(ctypes.byref(h), ctypes.byref(bad)) == dpso.ERR_ARG
     state = ctypes.c_int32(0)
     assert L.dpso_server_poll(None, 1, ctypes.byref(state), None, 0, None, None) == dpso.ERR_ARG

@@ -165,7 +165,7 @@ def test_shortest_first_admission_keeps_results():
     still the solo run's."""
     reqs = sorted(_requests(), key=lambda r: -r[0].n)[:6]  # largest first
     server = dpso.Server(dpso.default_server_params(max_active=2, generations_per_tick=4,
-                                                    policy=dpso.SERVE_SHORTEST_FIRST))
+                                                    policy=dpso.SERVE_SHORTEST_FIRST, lanes=1))
     ids = [server.submit(i.xyz, i.boxes, i.tags, cp, p, s, T) for i, cp, p, s, T in reqs]
     got = _wait_all(server, ids)
     for rid, req in zip(ids, reqs):
@@ -175,3 +175,34 @@ def test_shortest_first_admission_keeps_results():
     # the smallest request (submitted last) finished before the largest one
     assert lat[ids[-1]] < lat[ids[0]]
     server.close()
+
+
+@pytest.mark.parametrize("lanes", [1, 3, 8])
+def test_lanes_keep_results_and_let_small_requests_pass(lanes):
+    """Size-class lanes: every result is still the solo run's, with one lane
+    (a single lock-step batch) and with several; with several lanes a small
+    request submitted after a large one finishes first."""
+    reqs = _requests()
+    big = (inputs.random_instance(420, 3, 991), dpso.default_cost_params(),
+           dpso.default_params(swarm=512), 17, 300)
+    small = (inputs.random_instance(30, 1, 992), dpso.default_cost_params(),
+             dpso.default_params(swarm=32), 18, 10)
+    server = dpso.Server(dpso.default_server_params(generations_per_tick=4, lanes=lanes))
+    order = [big] + reqs + [small]
+    ids = [server.submit(i.xyz, i.boxes, i.tags, cp, p, s, T) for i, cp, p, s, T in order]
+    got = _wait_all(server, ids)
+    for rid, req in zip(ids, order):
+        wt, wc = _solo(req)
+        assert got[rid][1] == wc and np.array_equal(got[rid][0], wt), req[0].n
+    if lanes > 1:
+        assert server.poll(ids[-1])[3] < server.poll(ids[0])[3]
+    st = server.stats()
+    assert st["completed"] == len(order) and st["failed"] == 0 and st["memory_used_bytes"] == 0
+    server.close()
+
+
+def test_server_rejects_bad_lane_counts():
+    for lanes in (-1, 9):
+        with pytest.raises(dpso.DpsoError) as e:
+            dpso.Server(dpso.default_server_params(lanes=lanes))
+        assert e.value.status == dpso.ERR_ARG

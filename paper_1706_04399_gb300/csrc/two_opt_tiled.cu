@@ -251,9 +251,10 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
         constexpr bool segmode = SEG;
 
         // The subgroup stages the `count` cost rows of the tile starting at I:
-        // each warp posts kPerWarp rows, one bulk copy per lane (row r from
+        // warp w posts the kPerWarp rows of slot w - 1 (warp 0 the last slot,
+        // empty for most tile heights), one bulk copy per lane (row r from
         // shifted copy (r>>3)&3), so the copies are issued by several warps at
-        // once rather than one after another by one warp.  Lane 0 of warp 0
+        // once rather than one after another by one warp.  Lane 0 of one warp
         // arms the barrier with the tile's bytes afterwards (a copy that lands
         // before that only takes the transaction count below zero: the phase
         // still waits for that one arrival).  Offsets into the shifted copies
@@ -265,7 +266,7 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
             // the subgroup barrier before this ordered the generic reads of
             // the previous tile; this orders them before the async writes
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
-            const int r = wsg * kPerWarp + lane;
+            const int r = ((wsg + WSG - 1) % WSG) * kPerWarp + lane;
             if (lane < kPerWarp && r < count) {
                 const unsigned k = (r >> 3) & 3;
                 const unsigned off = (k * static_cast<unsigned>(n) + smu[xs16 + I + r]) * row_bytes;
@@ -405,7 +406,9 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                 const int rlast = seg ? min(min(I + kRows - 1, pb), n - 3)
                                       : (first || !segmode ? n - 3 : min(pa - 1, n - 3));
                 stage(I, count);
-                if (wsg == 0) {
+                // the barrier is armed by warp 0 for short tours (which first
+                // decides the tile's mode) and by the last warp for long ones
+                if (wsg == (segmode ? WSG - 1 : 0)) {
                     if (!segmode) {
                         // short tours: the tile's mode; a full tile starts its
                         // rows' keys afresh.  Both before the barrier arrival
@@ -456,8 +459,16 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                     cstop = min(n, pb + 1);
                 }
                 const int ngroups = cstop > cstart ? (cstop - cstart + 3) >> 2 : 0;
-                const int g0 = (ngroups * wsg) / WSG, g1 = (ngroups * (wsg + 1)) / WSG;
-                if (wsg == 0) {
+                // groups starting below I+kStaged hold the diagonal triangle
+                // (masked): one per lane group, so that none runs them alone
+                // while the rest of its warp waits; the other groups are split
+                // evenly, contiguous per warp and per lane group
+                const int nmask = min(ngroups, max(0, (I + kStaged - cstart + 3) >> 2));
+                const int nrest = ngroups - nmask;
+                const int cs2 = cstart + 4 * nmask;
+                const int g0 = (nrest * wsg) / WSG, g1 = (nrest * (wsg + 1)) / WSG;
+                // (the counting rotates over the warps, tile by tile)
+                if (wsg == t % WSG) {
                     // pairs (i, j), i+2 <= j <= n-1, (i, j) != (0, n-1), of the rows
                     // evaluated (in the columns cstart..E-1), and of the rows
                     // below pa against the segment's columns (segment tiles)
@@ -483,10 +494,8 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                     // first valid column of this lane's row (rows past rlast have none)
                     const int lim = eval_ok ? ie + 2 : INT_MAX;
                     int m = INT_MAX, cm = 0;
-                    int c = cstart + 4 * h0;
-                    const int cend = cstart + 4 * h1;
-                    int q = h0 < h1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
-                    const int4* rp = smi4 + ((rec2 + c) >> 1);   // records c .. c+3
+                    int c = 0, q = 0;
+                    const int4* rp = smi4;
                     auto group = [&](bool masked) {
                         const int4 ra4 = rp[0], rb4 = rp[1];
                         int v0 = at(r1, q) + at(r2, ra4.x) + ra4.y;
@@ -506,10 +515,19 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                         c += 4;
                         rp += 2;
                     };
-                    // groups starting below I+kStaged hold the diagonal triangle
-                    // (none on partial tiles)
-                    const int cmask = min(cend, I + kStaged);
-                    while (c < cmask) group(true);
+                    // this lane group's triangle groups first (its lowest
+                    // columns: the scan stays in increasing column order)
+                    constexpr int kGroups = WSG * SPLIT;
+                    for (int k = wsg * SPLIT + part; k < nmask; k += kGroups) {
+                        c = cstart + 4 * k;
+                        q = smi2[rec2 + c - 1].x;  // 4 x_c (c >= I + 1 >= 1)
+                        rp = smi4 + ((rec2 + c) >> 1);
+                        group(true);
+                    }
+                    c = cs2 + 4 * h0;
+                    const int cend = cs2 + 4 * h1;
+                    q = h0 < h1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
+                    rp = smi4 + ((rec2 + c) >> 1);           // records c .. c+3
                     // two groups at a time (sixteen gathers in flight) where the
                     // register budget allows it: one long tour per 8-warp CTA
                     constexpr bool kPairs = TPC == 1 && TG == 1 && ROWS <= 16;
@@ -593,37 +611,52 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                 }
                 if (SPLIT > 1 && seg && pa > 0) {
                     // (b) rows i < pa against this tile's segment columns
-                    // j = I + r, one row i per lane, r over the tile:
+                    // j = I + r, one row i per lane (blocks of 32 rows), r over
+                    // the tile:
                     //   delta(i, j) = C[x_j][x_i] + C[x_j+1][x_i+1] - C[x_i][x_i+1]
                     //                 - C[x_j][x_j+1]
                     // read from the staged rows r, r + 1 (their bases are the
                     // same on every lane), the lane keeping its smallest
-                    // negative delta and first r.  The pairs (pa - 1, pa) and
-                    // (0, n - 1) are not 2-opt moves; their delta is exactly 0
-                    // for a symmetric C, so they never enter the cache.
+                    // negative delta and first r.  The (block, r) units are split
+                    // evenly over the warps (a block's r range may be split
+                    // between two warps; both fold into the cache).  The pairs
+                    // (pa - 1, pa) and (0, n - 1) are not 2-opt moves; their
+                    // delta is exactly 0 for a symmetric C, so they never enter
+                    // the cache.
                     const int jn = min(kRows, pb - I + 1);
                     const int* const tb = smi + half * buf_words;
                     const int nblk = (pa + 31) >> 5;
-                    for (int blk = wsg; blk < nblk; blk += WSG) {
+                    int tjr[kRows];  // -C[x_j][x_j+1] of the tile's columns
+#pragma unroll
+                    for (int r = 0; r < kRows; ++r) tjr[r] = r < jn ? smi2[rec2 + I + r].y : 0;
+                    const int nu = nblk * jn;
+                    int u = (nu * wsg) / WSG;
+                    const int u1 = (nu * (wsg + 1)) / WSG;
+                    while (u < u1) {
+                        const int blk = u / jn;
+                        const int r0 = u - blk * jn;
+                        const int re = min(jn, r0 + (u1 - u));
                         const int i = (blk << 5) + lane;
                         const int ic = min(i, pa - 1);  // lanes past pa: a valid row, not kept
                         const int qi = smi2[rec2 + (ic > 0 ? ic - 1 : n - 1)].x;  // 4 x_i
                         const int2 ri = smi2[rec2 + ic];  // {4 x_i+1, -C[x_i][x_i+1]}
-                        int best = 0, br = 0;
+                        // kept while below -ri.y, i.e. while the delta is negative
+                        int best = -ri.y, br = 0;
 #pragma unroll
                         for (int r = 0; r < kRows; ++r) {
-                            if (r < jn) {
+                            if (r >= r0 && r < re) {
                                 const char* const ra_ =
                                     reinterpret_cast<const char*>(tb + r * ldq + ((r >> 3) & 3));
                                 const char* const rb_ = reinterpret_cast<const char*>(
                                     tb + (r + 1) * ldq + (((r + 1) >> 3) & 3));
-                                const int d = at(ra_, qi) + at(rb_, ri.x) + ri.y +
-                                              smi2[rec2 + I + r].y;
+                                const int d = at(ra_, qi) + at(rb_, ri.x) + tjr[r];
                                 br = d < best ? r : br;
                                 best = min(best, d);
                             }
                         }
-                        if (i < pa && best < 0) atomicMin(&rowkey[i], pack_key(best, i, I + br));
+                        if (i < pa && best < -ri.y)
+                            atomicMin(&rowkey[i], pack_key(best + ri.y, i, I + br));
+                        u += re - r0;
                     }
                 }
                 if (TG == 2 && wsg == 0 && lane == 0)

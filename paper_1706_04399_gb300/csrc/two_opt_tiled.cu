@@ -460,10 +460,14 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                 }
                 const int ngroups = cstop > cstart ? (cstop - cstart + 3) >> 2 : 0;
                 // groups starting below I+kStaged hold the diagonal triangle
-                // (masked): one per lane group, so that none runs them alone
-                // while the rest of its warp waits; the other groups are split
-                // evenly, contiguous per warp and per lane group
-                const int nmask = min(ngroups, max(0, (I + kStaged - cstart + 3) >> 2));
+                // (masked).  Where a warp splits into lane groups (8/16-row
+                // tiles) they go one per lane group, so that none runs them
+                // alone while the rest of its warp waits; the other groups are
+                // split evenly, contiguous per warp and per lane group.  With
+                // one row per lane they stay at the start of warp 0's range
+                // (a warp runs its masked groups instead of as many unmasked ones).
+                const int nmask =
+                    SPLIT > 1 ? min(ngroups, max(0, (I + kStaged - cstart + 3) >> 2)) : 0;
                 const int nrest = ngroups - nmask;
                 const int cs2 = cstart + 4 * nmask;
                 const int g0 = (nrest * wsg) / WSG, g1 = (nrest * (wsg + 1)) / WSG;
@@ -528,6 +532,10 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                     const int cend = cs2 + 4 * h1;
                     q = h0 < h1 ? smi2[rec2 + c - 1].x : 0;  // 4 x_c
                     rp = smi4 + ((rec2 + c) >> 1);           // records c .. c+3
+                    if constexpr (SPLIT == 1) {
+                        const int cmask = min(cend, I + kStaged);
+                        while (c < cmask) group(true);
+                    }
                     // two groups at a time (sixteen gathers in flight) where the
                     // register budget allows it: one long tour per 8-warp CTA
                     constexpr bool kPairs = TPC == 1 && TG == 1 && ROWS <= 16;

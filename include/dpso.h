@@ -176,7 +176,7 @@ int dpso_two_opt(const int32_t *C_dev, int32_t n, uint16_t *tours_dev, int32_t c
  * this is a deployment variant).  Same arguments, the same tours, costs,
  * pair and move counts, and the same synchronisation as dpso_two_opt, but it
  * always runs the general (untiled) 2-opt kernel, which is slower for tours
- * the tiled kernel takes (n <= 4168): the tiled kernel reads four row-shifted
+ * the tiled kernel takes (n <= 4145): the tiled kernel reads four row-shifted
  * copies of the cost matrix that would have to be allocated.  Its scratch --
  * error word, work queue, totals, the task descriptor and per-tour pass /
  * move counts -- lives in one fixed 128 KiB device array inside the library

@@ -18,7 +18,11 @@
 //    a+8, a+16, a+24 in the same bank.  The cost matrix is therefore kept in
 //    four copies whose rows are shifted right by 0..3 words; row a of a tile is
 //    taken from copy (a>>3)&3 into a row pitch ldq with ldq/4 odd, so the 32
-//    lanes reading one column hit 32 distinct banks.
+//    lanes reading one column hit 32 distinct banks.  Eight-row tiles need no shift
+//    (rows 0..8 at a pitch with pitch/4 odd already fall on distinct bank
+//    quads, row 8 serving only as a second row): their segment-tile kernels
+//    stage from copy 0 at a compile-time pitch class, so that a lane's two
+//    rows are a constant apart.
 //  * Column records rec[c] = {4 x_c+1, -C[x_c][x_c+1]} give the second
 //    gather's byte offset and the edge term in one broadcast load; the first
 //    gather's offset 4 x_c is the previous record's.
@@ -66,12 +70,30 @@ __global__ void shift_copies_kernel(const int* __restrict__ C, int ldc, int n, i
 
 }  // namespace
 
+// Tours of at least this many viewpoints use segment tiles (see the kernel).
+constexpr int kSegmentMinN = 512;
+
+// Compile-time pitches (words) of the staged rows of 8-row segment tiles with
+// one tour per CTA: 256 k + 4 for k = 2..16, each 4 times an odd number.
+constexpr int kPitchStep = 256, kPitchMin = 2, kPitchMax = 16;
+
+// The staged rows' pitch for tours of up to n viewpoints: the smallest
+// compile-time class holding a row for 8-row segment tiles with one tile in
+// flight (n >= kSegmentMinN; tours per CTA must be 1 for segment tiles, and a
+// larger class only costs shared memory elsewhere), else the row size itself.
+__host__ __device__ inline int staged_pitch(int n, int rows, int stages) {
+    const int ld = shifted_ld(n);
+    if (rows != 8 || stages != 1 || n < kSegmentMinN) return ld;
+    const int k = (ld - 4 + kPitchStep - 1) / kPitchStep;
+    return k <= kPitchMax ? kPitchStep * max(k, kPitchMin) + 4 : ld;
+}
+
 // Tiles of a tour's fixed tile grid (rows 0..n-3 in tiles of `rows`).
 __host__ __device__ inline int grid_tiles(int n, int rows) { return (n - 2 + rows - 1) / rows; }
 
 size_t two_opt_tiled_smem(int n, int rows_per_tile, int stages) {
-    const size_t rows =
-        static_cast<size_t>(stages) * (rows_per_tile + 1) * shifted_ld(n) * sizeof(int);
+    const size_t rows = static_cast<size_t>(stages) * (rows_per_tile + 1) *
+                        staged_pitch(n, rows_per_tile, stages) * sizeof(int);
     const size_t rec = static_cast<size_t>(n + 4) * sizeof(int2);
     const size_t xs = static_cast<size_t>((n + 1 + 7) / 8 * 8) * sizeof(uint16_t);
     // the row cache
@@ -91,8 +113,6 @@ namespace {
 // is at least 2^29 - 1 > 0, so padding never supplies an improving move.
 constexpr int kPadCost = (1 << 30) - 1;
 
-// Tours of at least this many viewpoints use segment tiles (see the kernel).
-constexpr int kSegmentMinN = 512;
 static_assert(2LL * DPSO_COST_MAX + kPadCost <= INT_MAX, "padding column overflows");
 static_assert(static_cast<long long>(kPadCost) - DPSO_COST_MAX > 0, "padding column improves");
 
@@ -149,11 +169,21 @@ constexpr int tiled_min_blocks() {
 // SEG: segment tiles (launches whose longest tour has n >= kSegmentMinN;
 // one tour per CTA), else partial tiles.  Each kernel holds only its own
 // mode's code: with both compiled in, short tours ran 6-10 % slower.
-template <int ROWS, int TPC, int TG, bool SEG>
+// PITCH: 0, or (8-row segment tiles, one tour per CTA) the staged rows' pitch
+// in words as a compile-time constant (a class at least the tour's row size,
+// PITCH/4 odd).  Nine rows at such a pitch need no word shift for conflict-
+// free columns (rows 0..7 fall on distinct bank quads, and row 8 only ever
+// serves as a lane's second row), so a lane's second row is its first plus a
+// constant and both gathers of a label share one address: C[x_i][y] at
+// r1 + 4y and C[x_i+1][y] at r1 + 4y + 4 PITCH.
+template <int ROWS, int TPC, int TG, bool SEG, int PITCH = 0>
 __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG>()))
     two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
     static_assert(!SEG || TPC == 1, "segment tiles are instantiated for one tour per CTA");
     static_assert(TG == 1 || TPC == 1, "two tile subgroups need the whole CTA");
+    static_assert(PITCH == 0 || (SEG && ROWS == 8 && TPC == 1 && TG == 1 && PITCH % 8 == 4),
+                  "a compile-time pitch is for 8-row segment tiles, 4 times an odd number");
+    constexpr int kPB = PITCH * 4;     // bytes from a staged row to the next (PITCH > 0)
     constexpr int kRows = ROWS;        // positions per tile, one per lane
     constexpr int kStaged = ROWS + 1;  // cost rows staged per tile
     // Tiles of 16 or 8 rows (long tours) split each warp into 2 or 4 lane
@@ -232,8 +262,9 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
             continue;
         }
         const int n = a.n;
-        const int ldq = shifted_ld(n);
-        const int buf_words = kStaged * ldq;
+        const int ldq = shifted_ld(n);                 // the row-shifted copies' pitch
+        const int spitch = PITCH > 0 ? PITCH : ldq;    // the staged rows' pitch
+        const int buf_words = kStaged * spitch;
         const int rec2 = TG * buf_words / 2;    // int2 index of record 0 (even)
         const int xs16 = (rec2 + n + 4) * 4;    // uint16 index of x_0
         // u64 index of the row cache, after the tour (n + 1 uint16, padded)
@@ -262,15 +293,16 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
         constexpr int kPerWarp = (kStaged + WSG - 1) / WSG;
         const unsigned tile_s = smem_addr(smi + half * buf_words);
         const unsigned row_bytes = static_cast<unsigned>(ldq) * 4u;
+        const unsigned slot_bytes = static_cast<unsigned>(spitch) * 4u;
         auto stage = [&](int I, int count) {
             // the subgroup barrier before this ordered the generic reads of
             // the previous tile; this orders them before the async writes
             asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
             const int r = ((wsg + WSG - 1) % WSG) * kPerWarp + lane;
             if (lane < kPerWarp && r < count) {
-                const unsigned k = (r >> 3) & 3;
+                const unsigned k = PITCH > 0 ? 0u : (r >> 3) & 3;
                 const unsigned off = (k * static_cast<unsigned>(n) + smu[xs16 + I + r]) * row_bytes;
-                bulk_row(tile_s + r * row_bytes, reinterpret_cast<const char*>(a.Cs) + off,
+                bulk_row(tile_s + r * slot_bytes, reinterpret_cast<const char*>(a.Cs) + off,
                          row_bytes, mbar);
             }
         };
@@ -366,7 +398,7 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
             if (segmode) group_sync<TPC>(grp);  // (short tours: full tiles reset their own rows)
             if (!first && segmode && warp == 0) {
                 // compact the need bitmask into a list (one warp; at most 32
-                // words: n <= 4168 tours have at most 521 grid tiles) and clear it
+                // words: n <= 4145 tours have at most 518 grid tiles) and clear it
                 const int nw = (ntiles + 31) / 32;
                 const unsigned bits = lane < nw ? needbits[lane] : 0u;
                 const int cnt = __popc(bits);
@@ -441,12 +473,22 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                 const int ie = I + lrow;
                 const bool eval_ok = (SPLIT > 1 || lane < kRows) && ie <= rlast;
                 const int ra = lrow, rb1 = lrow + 1;
-                const int p1 = half * buf_words + ra * ldq + ((ra >> 3) & 3);
-                const int p2 = half * buf_words + rb1 * ldq + ((rb1 >> 3) & 3);
+                const int shift1 = PITCH > 0 ? 0 : (ra >> 3) & 3;
+                const int shift2 = PITCH > 0 ? 0 : (rb1 >> 3) & 3;
+                const int p1 = half * buf_words + ra * spitch + shift1;
+                const int p2 = half * buf_words + rb1 * spitch + shift2;
                 const char* const r1 = reinterpret_cast<const char*>(smi + p1);
                 const char* const r2 = reinterpret_cast<const char*>(smi + p2);
                 auto at = [](const char* row, int off) {
                     return *reinterpret_cast<const int*>(row + off);
+                };
+                // the lane's second row at byte offset off (with a compile-time
+                // pitch: the first row's address of that label plus kPB)
+                auto at2 = [&](int off) {
+                    if constexpr (PITCH > 0)
+                        return *reinterpret_cast<const int*>((r1 + off) + kPB);
+                    else
+                        return at(r2, off);
                 };
                 // (a) the tile's rows over every column: groups of four from
                 // the even column at or below I+2 (records are read in pairs),
@@ -502,10 +544,10 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                     const int4* rp = smi4;
                     auto group = [&](bool masked) {
                         const int4 ra4 = rp[0], rb4 = rp[1];
-                        int v0 = at(r1, q) + at(r2, ra4.x) + ra4.y;
-                        int v1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w;
-                        int v2 = at(r1, ra4.z) + at(r2, rb4.x) + rb4.y;
-                        int v3 = at(r1, rb4.x) + at(r2, rb4.z) + rb4.w;
+                        int v0 = at(r1, q) + at2(ra4.x) + ra4.y;
+                        int v1 = at(r1, ra4.x) + at2(ra4.z) + ra4.w;
+                        int v2 = at(r1, ra4.z) + at2(rb4.x) + rb4.y;
+                        int v3 = at(r1, rb4.x) + at2(rb4.z) + rb4.w;
                         if (masked) {
                             v0 = c >= lim ? v0 : INT_MAX;
                             v1 = c + 1 >= lim ? v1 : INT_MAX;
@@ -541,14 +583,14 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                     constexpr bool kPairs = TPC == 1 && TG == 1 && ROWS <= 16;
                     while (kPairs && c + 4 < cend) {
                         const int4 ra4 = rp[0], rb4 = rp[1], rc4 = rp[2], rd4 = rp[3];
-                        const int v0 = at(r1, q) + at(r2, ra4.x) + ra4.y;
-                        const int v1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w;
-                        const int v2 = at(r1, ra4.z) + at(r2, rb4.x) + rb4.y;
-                        const int v3 = at(r1, rb4.x) + at(r2, rb4.z) + rb4.w;
-                        const int v4 = at(r1, rb4.z) + at(r2, rc4.x) + rc4.y;
-                        const int v5 = at(r1, rc4.x) + at(r2, rc4.z) + rc4.w;
-                        const int v6 = at(r1, rc4.z) + at(r2, rd4.x) + rd4.y;
-                        const int v7 = at(r1, rd4.x) + at(r2, rd4.z) + rd4.w;
+                        const int v0 = at(r1, q) + at2(ra4.x) + ra4.y;
+                        const int v1 = at(r1, ra4.x) + at2(ra4.z) + ra4.w;
+                        const int v2 = at(r1, ra4.z) + at2(rb4.x) + rb4.y;
+                        const int v3 = at(r1, rb4.x) + at2(rb4.z) + rb4.w;
+                        const int v4 = at(r1, rb4.z) + at2(rc4.x) + rc4.y;
+                        const int v5 = at(r1, rc4.x) + at2(rc4.z) + rc4.w;
+                        const int v6 = at(r1, rc4.z) + at2(rd4.x) + rd4.y;
+                        const int v7 = at(r1, rd4.x) + at2(rd4.z) + rd4.w;
                         const int ma = min(min(v0, v1), min(v2, v3));
                         const int mb = min(min(v4, v5), min(v6, v7));
                         cm = ma < m ? c : cm;
@@ -593,10 +635,10 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                         const int i0 = 4 * gi;
                         const int4 ra4 = rq[0], rb4 = rq[1];
                         rq += 2;
-                        int d0 = at(r1, q) + at(r2, ra4.x) + ra4.y + tj;
-                        int d1 = at(r1, ra4.x) + at(r2, ra4.z) + ra4.w + tj;
-                        int d2 = at(r1, ra4.z) + at(r2, rb4.x) + rb4.y + tj;
-                        int d3 = at(r1, rb4.x) + at(r2, rb4.z) + rb4.w + tj;
+                        int d0 = at(r1, q) + at2(ra4.x) + ra4.y + tj;
+                        int d1 = at(r1, ra4.x) + at2(ra4.z) + ra4.w + tj;
+                        int d2 = at(r1, ra4.z) + at2(rb4.x) + rb4.y + tj;
+                        int d3 = at(r1, rb4.x) + at2(rb4.z) + rb4.w + tj;
                         q = rb4.z;
                         d0 = jok ? d0 : INT_MAX;
                         d1 = jok && i0 + 1 < pa ? d1 : INT_MAX;
@@ -650,14 +692,24 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
                         const int2 ri = smi2[rec2 + ic];  // {4 x_i+1, -C[x_i][x_i+1]}
                         // kept while below -ri.y, i.e. while the delta is negative
                         int best = -ri.y, br = 0;
+                        // (with a compile-time pitch: two addresses per lane,
+                        // every staged row at a constant offset from them)
+                        const char* const bq = reinterpret_cast<const char*>(tb) + qi;
+                        const char* const bx = reinterpret_cast<const char*>(tb) + ri.x;
 #pragma unroll
                         for (int r = 0; r < kRows; ++r) {
                             if (r >= r0 && r < re) {
-                                const char* const ra_ =
-                                    reinterpret_cast<const char*>(tb + r * ldq + ((r >> 3) & 3));
-                                const char* const rb_ = reinterpret_cast<const char*>(
-                                    tb + (r + 1) * ldq + (((r + 1) >> 3) & 3));
-                                const int d = at(ra_, qi) + at(rb_, ri.x) + tjr[r];
+                                int d;
+                                if constexpr (PITCH > 0) {
+                                    d = *reinterpret_cast<const int*>(bq + r * kPB) +
+                                        *reinterpret_cast<const int*>(bx + (r + 1) * kPB) + tjr[r];
+                                } else {
+                                    const char* const ra_ = reinterpret_cast<const char*>(
+                                        tb + r * spitch + ((r >> 3) & 3));
+                                    const char* const rb_ = reinterpret_cast<const char*>(
+                                        tb + (r + 1) * spitch + (((r + 1) >> 3) & 3));
+                                    d = at(ra_, qi) + at(rb_, ri.x) + tjr[r];
+                                }
                                 br = d < best ? r : br;
                                 best = min(best, d);
                             }
@@ -775,11 +827,11 @@ size_t group_bytes(int n, int rows, int tg) {
     return (two_opt_tiled_smem(n, rows, tg) + 127) / 128 * 128;
 }
 
-template <int ROWS, int TPC, int TG, bool SEG>
+template <int ROWS, int TPC, int TG, bool SEG, int PITCH = 0>
 cudaError_t launch_cfg(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     const size_t gb = group_bytes(b.max_n, ROWS, TG);
     const size_t smem = gb * TPC;
-    auto* kern = two_opt_tiled_kernel<ROWS, TPC, TG, SEG>;
+    auto* kern = two_opt_tiled_kernel<ROWS, TPC, TG, SEG, PITCH>;
     cudaError_t e = raise_smem_limit(kern, smem);
     if (e != cudaSuccess) return e;
     int per_sm = 0;
@@ -789,6 +841,18 @@ cudaError_t launch_cfg(const TwoOptBatch& b, int num_sms, cudaStream_t st) {
     const int grid = max(1, min((b.total + TPC - 1) / TPC, per_sm * num_sms));
     kern<<<grid, kThreads * TG, smem, st>>>(b, static_cast<int>(gb / sizeof(int)));
     return cudaGetLastError();
+}
+
+// 8-row segment tiles, one tour per CTA: the instantiation of the launch's
+// pitch class (the runtime pitch when the tours are longer than every class).
+template <int K>
+cudaError_t launch_pitch(const TwoOptBatch& b, int pitch, int num_sms, cudaStream_t st) {
+    if (pitch == kPitchStep * K + 4) return launch_cfg<8, 1, 1, true, kPitchStep * K + 4>(b, num_sms, st);
+    if constexpr (K < kPitchMax) {
+        return launch_pitch<K + 1>(b, pitch, num_sms, st);
+    } else {
+        return launch_cfg<8, 1, 1, true>(b, num_sms, st);
+    }
 }
 
 // Launches with segment tiles (for every tour) when the launch holds a tour
@@ -805,6 +869,9 @@ cudaError_t launch_rows(const TwoOptBatch& b, int tpc, int tg, int num_sms, cuda
     }
     switch (tpc) {
         case 1:
+            if constexpr (ROWS == 8) {
+                if (seg) return launch_pitch<kPitchMin>(b, staged_pitch(b.max_n, 8, 1), num_sms, st);
+            }
             return seg ? launch_cfg<ROWS, 1, 1, true>(b, num_sms, st)
                        : launch_cfg<ROWS, 1, 1, false>(b, num_sms, st);
         case 2: return launch_cfg<ROWS, 2, 1, false>(b, num_sms, st);

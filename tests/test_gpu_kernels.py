@@ -178,8 +178,8 @@ def test_two_opt_large_tiles_capped_bitwise(n, moves):
 
 
 def test_two_opt_long_tours_two_per_cta_bitwise():
-    # 1906 <= n <= 2081 with at least two tours per SM takes 8-row tiles, two
-    # tours per CTA and four lane groups per warp by default; capped moves keep
+    # 1904 <= n <= 2049 with at least two tours per SM takes 8-row tiles, one
+    # tour per CTA and four lane groups per warp by default; capped moves keep
     # the oracle to a few passes per tour
     n, count = 1992, 320
     C_np = inputs.random_cost_matrix(n, 19, hi=1_000_000)

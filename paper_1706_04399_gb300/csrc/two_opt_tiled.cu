@@ -18,11 +18,11 @@
 //    a+8, a+16, a+24 in the same bank.  The cost matrix is therefore kept in
 //    four copies whose rows are shifted right by 0..3 words; row a of a tile is
 //    taken from copy (a>>3)&3 into a row pitch ldq with ldq/4 odd, so the 32
-//    lanes reading one column hit 32 distinct banks.  Eight-row tiles need no shift
-//    (rows 0..8 at a pitch with pitch/4 odd already fall on distinct bank
-//    quads, row 8 serving only as a second row): their segment-tile kernels
-//    stage from copy 0 at a compile-time pitch class, so that a lane's two
-//    rows are a constant apart.
+//    lanes reading one column hit 32 distinct banks.  Eight-row tiles need no
+//    shift (at a pitch with pitch/4 odd, rows 0..7, and rows 1..8, each fall
+//    on distinct bank quads; a lane reads rows r and r + 1): their
+//    segment-tile kernels stage from copy 0 at a compile-time pitch class, so
+//    that a lane's two rows are a constant apart.
 //  * Column records rec[c] = {4 x_c+1, -C[x_c][x_c+1]} give the second
 //    gather's byte offset and the edge term in one broadcast load; the first
 //    gather's offset 4 x_c is the previous record's.
@@ -172,10 +172,10 @@ constexpr int tiled_min_blocks() {
 // PITCH: 0, or (8-row segment tiles, one tour per CTA) the staged rows' pitch
 // in words as a compile-time constant (a class at least the tour's row size,
 // PITCH/4 odd).  Nine rows at such a pitch need no word shift for conflict-
-// free columns (rows 0..7 fall on distinct bank quads, and row 8 only ever
-// serves as a lane's second row), so a lane's second row is its first plus a
-// constant and both gathers of a label share one address: C[x_i][y] at
-// r1 + 4y and C[x_i+1][y] at r1 + 4y + 4 PITCH.
+// free columns (rows 0..7, and rows 1..8, each fall on distinct bank quads;
+// row 8 only ever serves as a lane's second row), so a lane's second row is
+// its first plus a constant and both gathers of a label share one address:
+// C[x_i][y] at r1 + 4y and C[x_i+1][y] at r1 + 4y + 4 PITCH.
 template <int ROWS, int TPC, int TG, bool SEG, int PITCH = 0>
 __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG>()))
     two_opt_tiled_kernel(TwoOptBatch b, int group_words) {
@@ -194,7 +194,7 @@ __global__ void __launch_bounds__(kThreads * TG, (tiled_min_blocks<ROWS, TPC, TG
     constexpr int WSG = WPT / TG;           // warps per tile subgroup
     constexpr int GT = WPT * 32;            // threads per tour
     // A group's shared slice seen through three element types (all alias its
-    // start): TG tile buffers of kStaged x ldq ints, then the column records
+    // start): TG tile buffers of kStaged x (staged pitch) ints, then the column records
     // (n + 4 int2, the last four padding), then the tour (n + 1 uint16).
     // Offsets depend on the tour's n; slices are sized for the largest n.
     extern __shared__ __align__(128) int sm_all[];
